@@ -1,0 +1,99 @@
+/*
+ * FP64 CPU oracle for the FUSE-Flow per-frame fusion path (arXiv 2602.01035).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code, header,
+ * table or constant with the CUDA path and must never be used as a fallback for it.
+ *
+ * Every quantity is computed in double precision, step by step in the order of the
+ * paper: Eq. 8 back-projection, Eq. 9 gating, Eq. 4-7 distance consistency, Eq. 10
+ * joint weight, Sec. II.5(1) adaptive partition, Sec. II.5(2)a representative,
+ * Eq. 11 weighted fusion.  The readings taken where the paper is silent are listed
+ * at each function in fuseflow_oracle.c.
+ */
+#ifndef FUSEFLOW_ORACLE_H
+#define FUSEFLOW_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_DEPTH_U16 = 0, ORC_DEPTH_F32 = 1, ORC_DEPTH_F64 = 2 };
+
+/* Pinhole intrinsics K_i and camera-from-world pose T_i (x_cam = R x_world + t). */
+typedef struct {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+    double R[9]; /* row-major */
+    double t[3];
+} orc_camera;
+
+typedef struct {
+    float tau;             /* Eq. 9 threshold, compared in float32 */
+    int32_t k_views;       /* K of Eq. 7, counting camera i itself */
+    double sigma_m;        /* sigma of Eq. 7, metres */
+    double coarse_cell_m;  /* edge of the coarse grid cell, metres */
+    int32_t max_level;     /* finest refinement level */
+    int32_t n_min;         /* density threshold of level 0 */
+    int32_t depth_format;  /* ORC_DEPTH_* */
+    int32_t use_conf;      /* 0: no measurement confidence (no gate, omega = V) */
+    double depth_scale;    /* metres per depth unit */
+    int32_t use_consistency; /* 0: V = 1 */
+    int32_t row_step;      /* process rows y % row_step == 0 only (timing samples); 1 = all */
+    double band_m;         /* report points within band_m of a cell boundary */
+    double band_px;        /* report projections within band_px of a half-pixel tie */
+    double band_az;        /* report projections with |a_z| below band_az metres */
+} orc_params;
+
+/* Per-pixel outputs, arrays of n_pixels entries in global pixel order
+ * g = off_i + y * W_i + x.  Any pointer may be NULL. */
+typedef struct {
+    uint8_t *valid, *gated, *in_range;
+    double *pw;           /* [n][3] world point P_i(x, y), metres (gated pixels) */
+    double *e;            /* exponent of Eq. 7: sum_j d_ij^2 / sigma^2 / (K-1) */
+    double *omega;        /* Eq. 10 */
+    double *log_omega;    /* ln(omega), finite even when omega underflows */
+    int32_t *nview;       /* number of views entering the sum of Eq. 7 */
+    uint64_t *key;        /* cell key, ~0 if not gated or out of range */
+    int32_t *level;       /* refinement level of the point's coarse cell, -1 if none */
+    double *margin_cell_m;/* distance to the nearest boundary of the point's cell, metres */
+    double *margin_tie_px;/* min over views of the distance of u+1/2, v+1/2 to an integer */
+    double *min_az;       /* min over views of |a_z| (metres) */
+} orc_points;
+
+/* Per-cell outputs ordered by representative pixel index, ascending. */
+typedef struct {
+    uint64_t *key;
+    uint32_t *count, *rep;
+    double *weight;       /* W = sum of member omegas */
+    double *pos;          /* [n][3] fused position, metres */
+    double *rgb;          /* [n][3] fused colour, 0..255 */
+    uint32_t *flags;      /* ORC_CELL_* */
+} orc_cells;
+
+enum { ORC_CELL_BOUNDARY = 1, ORC_CELL_AMBIGUOUS_LEVEL = 2, ORC_CELL_TIE = 4 };
+
+typedef struct {
+    int64_t n_valid, n_gated, n_out_of_range, n_cells;
+    double bbox[6];        /* min xyz, max xyz over gated points; +inf/-inf if none */
+    int64_t n_boundary_points, n_tie_points, n_ambiguous_coarse, n_coarse;
+} orc_stats;
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NOMEM = 2, ORC_ERR_CAPACITY = 3 };
+
+void orc_default_params(orc_params *p);
+
+/* Static neighbour table: for each camera the K-1 other cameras used in Eq. 7. */
+int orc_neighbours(const orc_camera *cams, int32_t n_cams, int32_t k_views, int32_t *out);
+
+int orc_fuse_frame(const orc_camera *cams, int32_t n_cams, const orc_params *p,
+                   const void *const *depth, const float *const *conf,
+                   const uint8_t *const *rgb, orc_points *pts, orc_cells *cells,
+                   int64_t cell_capacity, orc_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
