@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FUSE-Flow per-frame fusion path on GB300.
+
+Workload: the 8-camera 1280x720 rig (uint16 depth in mm, float32 confidence, uint8 RGB),
+300 frames per step as in the 300-frame sequence of that rig.  A pool of distinct seeded
+frames (larger than L2) is cycled, so every frame is re-read from HBM.  One step fuses the
+300 frames through the C ABI, one frame per fuse call.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle (the only
+reference implementation of the method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "depth px/s and frames/s at 8x1280x720 views; p50/p99 latency, served vs plain"
+KERNELS_PER_FRAME = 6      # count, assign, accumulate, scan words, scan blocks, emit
+CELL_OUT_BYTES = 44        # pos 12 + rgb 12 + weight 4 + count 4 + rep 4 + key 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames-per-step", type=int, default=300)
+    ap.add_argument("--pool", type=int, default=8, help="distinct frames cycled (> L2 in total)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-frames", type=int, default=64)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.strip().split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_pool(n_frames: int, first: int):
+    from paper_2602_01035_gb300 import scenes as S
+    cache = {}
+    frames = []
+    rig = None
+    for k in range(n_frames):
+        rig, _, fr = S.config3(frame=first + k, cache=cache)
+        frames.append(fr)
+    return rig, frames
+
+
+def roofline_model(stage: str, px: int, cells: float, depth_bytes: int):
+    """Algorithmic bytes of one launch of each stage (inputs read once, outputs written once)."""
+    if stage == "count":
+        return depth_bytes * px + 4 * px            # depth + confidence
+    if stage == "assign":
+        return depth_bytes * px + 4 * px            # depth + confidence (gathers hit L2)
+    if stage == "accumulate":
+        return depth_bytes * px + 3 * px            # depth + colour
+    if stage == "emit":
+        return CELL_OUT_BYTES * cells
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2602_01035_gb300 import fuseflow as F
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    rig, pool = make_pool(args.pool, first=rank * args.pool)
+    px = rig.n_pixels
+    frame_bytes = pool[0].input_bytes()
+    dtensors = []
+    for fr in pool:
+        d = [torch.from_numpy(x).to(dev) for x in fr.depth]
+        c = [torch.from_numpy(x).to(dev) for x in fr.conf]
+        r = [torch.from_numpy(x).to(dev) for x in fr.rgb]
+        dtensors.append((d, c, r, [t.data_ptr() for t in d], [t.data_ptr() for t in c],
+                         [t.data_ptr() for t in r]))
+    ff = F.FuseFlow(rig)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    FPS = args.frames_per_step
+
+    def step():
+        for i in range(FPS):
+            t = dtensors[i % len(dtensors)]
+            F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], sh)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    status, st = ff.stats(sh, check=False)
+    if status != F.FUSEFLOW_OK:
+        raise RuntimeError(f"fusion failed during warm-up: {F.fuseflow_status_string(status)}")
+    n_cells = st.n_cells
+
+    # ------------------------------------------------------------ timed region
+    clk = ClockSampler(local_rank)
+    clk.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    status, st = ff.stats(sh, check=False)
+    ok_status = status == F.FUSEFLOW_OK
+
+    total_frames = world * args.steps * FPS
+    value = total_frames * px / (ms / 1e3)
+    fps = total_frames / (ms / 1e3)
+
+    # ------------------------------------------------------------ per-frame latency (plain path)
+    lat = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(min(FPS, 300))]
+    for i, (a, b) in enumerate(evs):
+        t = dtensors[i % len(dtensors)]
+        a.record(stream)
+        F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], sh)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    lat = sorted(a.elapsed_time(b) for a, b in evs)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+
+    # ------------------------------------------------------------ per-stage times (roofline)
+    F.fuseflow_enable_stage_timing(ff.ctx, True)
+    n_stage_frames = min(FPS, 256)
+    for i in range(n_stage_frames):
+        t = dtensors[i % len(dtensors)]
+        F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], sh)
+    stage_ms, n_timed = F.fuseflow_read_stage_times(ff.ctx)
+    F.fuseflow_enable_stage_timing(ff.ctx, False)
+    stage_avg = {k: v / max(n_timed, 1) for k, v in stage_ms.items()}
+    dominant = max(stage_avg, key=stage_avg.get)
+    peak, peak_kind = load_peaks()
+    depth_bytes = 2
+    alg = roofline_model(dominant, px, n_cells, depth_bytes)
+    roof = None
+    if alg is not None:
+        achieved = alg / (stage_avg[dominant] / 1e3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(alg),
+                "launch_ms": round(stage_avg[dominant], 5)}
+    path_bytes = 9 * px + CELL_OUT_BYTES * n_cells
+    frame_ms = sum(stage_avg.values())
+    path_roof = {"bytes_per_frame": int(path_bytes), "frame_ms_staged": round(frame_ms, 5),
+                 "achieved_gbs": round(path_bytes / (ms / 1e3 / (args.steps * FPS)) / 1e9, 1),
+                 "frac": round(path_bytes / (ms / 1e3 / (args.steps * FPS)) / 1e9 / peak, 4)}
+
+    # ------------------------------------------------------------ end to end (host buffers)
+    e2e = None
+    n_e2e = min(args.e2e_frames, FPS)
+    pinned = []
+    for fr in pool:
+        d = [torch.from_numpy(x).pin_memory() for x in fr.depth]
+        c = [torch.from_numpy(x).pin_memory() for x in fr.conf]
+        r = [torch.from_numpy(x).pin_memory() for x in fr.rgb]
+        pinned.append((d, c, r))
+    cap = ff.capacity
+    outs = [torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
+            torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
+            torch.empty(cap, dtype=torch.float32).pin_memory(),
+            torch.empty(cap, dtype=torch.int32).pin_memory(),
+            torch.empty(cap, dtype=torch.int32).pin_memory(),
+            torch.empty(cap, dtype=torch.int64).pin_memory()]
+    optr = [o.data_ptr() for o in outs]
+
+    def host_frame(i):
+        d, c, r = pinned[i % len(pinned)]
+        return F.fuseflow_fuse_frame_host(ff.ctx, [t.data_ptr() for t in d], [t.data_ptr() for t in c],
+                                          [t.data_ptr() for t in r], *optr, sh)
+
+    for i in range(3):
+        host_frame(i)
+    d2h = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        s_, st_ = host_frame(i)
+        d2h += st_.n_cells * CELL_OUT_BYTES + 48
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    e2e = {"value": round(n_e2e * px / e2e_s * world, 1), "unit": "px/s",
+           "frames_per_s": round(n_e2e / e2e_s * world, 2),
+           "h2d_bytes_per_step": int(frame_bytes * FPS),
+           "d2h_bytes_per_step": int(d2h / n_e2e * FPS),
+           "frames_timed": n_e2e, "entry_point": "fuseflow_fuse_frame_host"}
+
+    # ------------------------------------------------------------ CPU baseline (oracle)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(rig, pool[:2])
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "px/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "8x1280x720 rig: uint16 depth (mm), float32 confidence, uint8 RGB; "
+                               f"{FPS} frames per step, one frame per fuse call",
+                   "n_cams": 8, "width": 1280, "height": 720, "frames_per_step": FPS,
+                   "pool_frames": len(pool), "pool_bytes": int(frame_bytes * len(pool)),
+                   "l2": "inputs larger than L2: a pool of distinct frames is cycled, each frame "
+                         "re-read only after the others",
+                   "parallelism": f"replicas x{world}"},
+        "frames_per_s": round(fps, 2),
+        "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5), "path": "plain, one frame per launch sequence"},
+        "roofline": roof, "path_roofline": path_roof,
+        "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
+        "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
+        "cells_per_frame": int(n_cells), "status_ok": ok_status,
+        "clocks": clocks, "cpu_baseline": cpu,
+    }
+    ff.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def cpu_baseline(rig, frames, row_step=1):
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    n = 0
+    for fr in frames:
+        oracle.fuse_frame(rig, fr, {"row_step": row_step}, points=False)
+        n += rig.n_pixels // row_step
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 1), "unit": "px/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(frames)} frame(s) of the 8x1280x720 rig, rows y % {row_step} == 0 "
+                      f"back-projected ({n} px), {dt:.1f} s on one host core"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    from paper_2602_01035_gb300 import scenes as S
+    rig, _, fr = S.config3(frame=0)
+    row_step = 8
+    px = rig.n_pixels // row_step
+    for _ in range(args.warmup):
+        oracle.fuse_frame(rig, fr, {"row_step": row_step}, points=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fuse_frame(rig, fr, {"row_step": row_step}, points=False)
+    dt = time.perf_counter() - t0
+    value = args.steps * px / dt
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "px/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "8x1280x720 rig: uint16 depth (mm), float32 confidence, uint8 RGB; "
+                               "each step fuses a row sample of one frame on the host",
+                   "n_cams": 8, "width": 1280, "height": 720, "parallelism": "host, 1 core"},
+        "cpu_baseline": {"value": round(value, 1), "unit": "px/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: rows y % {row_step} == 0 of one 8x1280x720 frame "
+                                   f"({px} px), all 8 depth maps used by the consistency views"},
+        "e2e": {"value": round(value, 1), "unit": "px/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * fuseflow.h - C ABI of the GB300 (sm_103a) FUSE-Flow per-frame fusion path.
+ *
+ * Method: "FUSE-Flow: Scalable Real-Time Multi-View Point Cloud Reconstruction Using
+ * Confidence" (arXiv 2602.01035).  One call fuses the N RGB-D images of one time step
+ * (problem statement, Sec. II.1, Eq. 1) into a point cloud with one fused point per
+ * adaptive spatial-hash cell:
+ *   (a) back-projection of every valid pixel and confidence gating (Eq. 8, Eq. 9),
+ *   (b) joint weight = confidence x 3D distance consistency (Eq. 4-7, Eq. 10),
+ *   (c) adaptive spatial hash: coarse density, level per coarse cell, cell keys
+ *       (Sec. II.5(1) a-e),
+ *   (d) one representative per cell (largest confidence, Sec. II.5(2)a) and the
+ *       confidence-weighted fused position and colour of all members (Eq. 11).
+ *
+ * Conventions
+ *   - Pixel (x, y) of camera i has its centre at integer coordinates; depth is z-depth.
+ *   - Global pixel index g = off_i + y * W_i + x, off_i = sum_{k<i} W_k H_k.
+ *   - Pose: x_cam = R x_world + t (camera-from-world T_i; Eq. 8 applies T_i^-1).
+ *   - All image buffers are contiguous row-major, one buffer per camera.
+ *   - Every entry point returns a fuseflow_status; nothing aborts or exits.
+ *   - A context is not thread-safe: use one context per rig and per host thread.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ */
+#ifndef FUSEFLOW_H
+#define FUSEFLOW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FUSEFLOW_OK = 0,
+    FUSEFLOW_ERR_INVALID_ARG = 1,   /* null pointer, bad size or parameter */
+    FUSEFLOW_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+    FUSEFLOW_ERR_CAPACITY = 3,      /* more cells than max_cells, or a hash table filled up */
+    FUSEFLOW_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    FUSEFLOW_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    FUSEFLOW_ERR_INTERNAL = 6       /* a device-side consistency check failed */
+} fuseflow_status;
+
+typedef enum {
+    FUSEFLOW_DEPTH_U16 = 0,  /* uint16 depth units (e.g. millimetres), 0 = invalid */
+    FUSEFLOW_DEPTH_F32 = 1   /* float32 depth units, invalid unless > 0 and finite */
+} fuseflow_depth_format;
+
+/* Pinhole intrinsics K_i (Sec. II.1; the paper names no distortion model). */
+typedef struct {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+} fuseflow_intrinsics;
+
+/* Extrinsic pose T_i, camera-from-world: x_cam = R x_world + t, R row-major, t metres. */
+typedef struct {
+    double R[9];
+    double t[3];
+} fuseflow_extrinsics;
+
+/* Method parameters.  Start from fuseflow_default_params(). */
+typedef struct {
+    float tau;              /* Eq. 9 gate: a pixel is kept iff C > tau (float32 compare); 0.6 */
+    int32_t k_views;        /* K of Eq. 7 counting camera i; effective K = min(k_views, N); 4 */
+    double sigma_m;         /* sigma of Eq. 7 in metres (unspecified in the paper); 0.03 */
+    double coarse_cell_m;   /* coarse grid edge s0 (Sec. II.5(1)c) in metres; 0.32 */
+    int32_t max_level;      /* finest level Lmax, cell edge s0 / 2^Lmax; 4 (0 <= Lmax <= 14) */
+    int32_t n_min;          /* level l needs n_c >= n_min * 4^l points in the coarse cell; 32 */
+    int32_t depth_format;   /* fuseflow_depth_format */
+    int32_t use_conf;       /* 0 = ablation "no measurement confidence": no gate, omega = V */
+    double depth_scale;     /* metres per depth unit; 0.001 for millimetre uint16 */
+    int32_t use_consistency;/* 0 = ablation "no distance consistency": V = 1 */
+    int32_t reserved0;
+    int64_t max_cells;      /* output capacity in cells; 0 = half the rig's pixel count */
+} fuseflow_params;
+
+/* Frame statistics; written on the device by fuseflow_fuse_frame. */
+typedef struct {
+    int64_t n_valid;        /* pixels with valid depth */
+    int64_t n_gated;        /* pixels kept by the Eq. 9 gate */
+    int64_t n_out_of_range; /* gated points whose finest cell index leaves [-2^19, 2^19) */
+    int64_t n_cells;        /* cells of the fused cloud */
+    float bbox[6];          /* min xyz, max xyz of the gated points (Sec. II.5(1)b), metres */
+    int32_t error;          /* device error bits, 0 if none (see fuseflow_read_stats) */
+    int32_t n_coarse;       /* occupied coarse cells */
+} fuseflow_stats;
+
+/* Fused cloud: device arrays owned by the context, valid until the next fuse call on the
+ * same context or fuseflow_destroy.  Cells are ordered by representative pixel index,
+ * ascending; only the first stats->n_cells entries are meaningful. */
+typedef struct {
+    fuseflow_stats *stats;  /* device pointer */
+    float *pos;             /* [capacity][3] fused position (Eq. 11, normalised), metres */
+    float *rgb;             /* [capacity][3] fused colour, 0..255 */
+    float *weight;          /* [capacity] W = sum of the members' omega (Eq. 10) */
+    uint32_t *count;        /* [capacity] members per cell */
+    uint32_t *rep;          /* [capacity] representative's global pixel index */
+    uint64_t *key;          /* [capacity] level << 60 | (kx+2^19) << 40 | (ky+2^19) << 20 | (kz+2^19) */
+    int64_t capacity;       /* = max_cells */
+} fuseflow_cloud;
+
+/* Optional per-pixel trace of the last fused frame (caller-owned device arrays of
+ * n_pixels entries; any pointer may be NULL).  Pixels that are not gated get
+ * nview = -1, key = ~0 and NaN in the float arrays. */
+typedef struct {
+    float *pw;              /* [n][3] world point of Eq. 8, metres */
+    float *omega;           /* Eq. 10 joint weight (may underflow to 0 in float32) */
+    float *e;               /* exponent of Eq. 7, sum_j d_ij^2 / sigma^2 / (K-1) */
+    int32_t *nview;         /* views that entered the sum of Eq. 7 */
+    uint64_t *key;          /* cell key, ~0 if not gated or out of range */
+} fuseflow_trace;
+
+typedef struct fuseflow_ctx fuseflow_ctx;
+
+/* Fills *p with the defaults listed above.  tau = 0.6 is Eq. 9's printed value. */
+void fuseflow_default_params(fuseflow_params *p);
+
+/* Creates a context for a rig of n_cams cameras (1 <= n_cams <= 64; K-1 <= 8).
+ * Host arrays intr[n_cams], extr[n_cams] are copied; the context precomputes the
+ * relative poses T_ji = T_j T_i^-1 of Eq. 4 in double precision, the static neighbour
+ * table of Sec. II.5(2)b, and allocates its device tables on the current device.
+ * Returns INVALID_ARG for bad sizes or parameters, OUT_OF_MEMORY, CUDA. */
+int fuseflow_create(const fuseflow_intrinsics *intr, const fuseflow_extrinsics *extr,
+                    int32_t n_cams, const fuseflow_params *params, fuseflow_ctx **out);
+
+/* Releases every device and host resource of the context (NULL is a no-op). */
+void fuseflow_destroy(fuseflow_ctx *ctx);
+
+/* Fuses one frame (steps (a)-(d) above), asynchronously on `stream`.
+ * depth[i], conf[i], rgb[i] are caller-owned DEVICE pointers to camera i's images
+ * (depth: uint16 or float32 per params; conf: float32 in [0,1] (Eq. 2); rgb: uint8x3
+ * interleaved), valid until the stream reaches the end of this call's work.
+ * *out receives the context-owned output arrays.  Capacity overflows and device-side
+ * failures are reported by the next fuseflow_read_stats.  Returns INVALID_ARG, CUDA. */
+int fuseflow_fuse_frame(fuseflow_ctx *ctx, const void *const *depth, const float *const *conf,
+                        const uint8_t *const *rgb, fuseflow_cloud *out, void *stream);
+
+/* Waits for `stream`, copies the last frame's statistics to *host_stats and returns
+ * CAPACITY if the frame overflowed max_cells or a hash table, INTERNAL if a device-side
+ * check failed, OK otherwise. */
+int fuseflow_read_stats(fuseflow_ctx *ctx, fuseflow_stats *host_stats, void *stream);
+
+/* End-to-end variant on HOST buffers: copies the images host-to-device (pinned memory
+ * gives asynchronous copies), fuses, waits, and copies the first n_cells cells into the
+ * caller's host arrays (each sized for max_cells; any may be NULL).  Synchronous.
+ * Returns the status of fuseflow_read_stats. */
+int fuseflow_fuse_frame_host(fuseflow_ctx *ctx, const void *const *depth,
+                             const float *const *conf, const uint8_t *const *rgb,
+                             float *pos, float *rgb_out, float *weight, uint32_t *count,
+                             uint32_t *rep, uint64_t *key, fuseflow_stats *host_stats,
+                             void *stream);
+
+/* Registers (or, with NULL, clears) a per-pixel trace written by later fuse calls. */
+int fuseflow_set_trace(fuseflow_ctx *ctx, const fuseflow_trace *trace);
+
+/* Copies the static neighbour table (n_cams rows of K-1 camera indices) to host `out`
+ * (n_cams * (K-1) entries) and K-1 to *k_minus_1. */
+int fuseflow_get_neighbours(const fuseflow_ctx *ctx, int32_t *out, int32_t *k_minus_1);
+
+/* Per-stage device timing for profiling.  While enabled, every fuse call records CUDA
+ * events between its stages on its own stream (a ring of the last 1024 frames).
+ * fuseflow_read_stage_times waits for the last recorded event, writes the summed
+ * milliseconds of each of the FUSEFLOW_N_STAGES stages to ms[] and the number of frames
+ * to *n_frames, then resets the ring.  Stages: 0 clear, 1 count (a), 2 assign (b, c),
+ * 3 accumulate (d), 4 scan, 5 emit. */
+#define FUSEFLOW_N_STAGES 6
+int fuseflow_enable_stage_timing(fuseflow_ctx *ctx, int enable);
+int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
+const char *fuseflow_stage_name(int stage);
+
+/* Number of pixels of the rig (sum of W_i H_i) and the output capacity. */
+int64_t fuseflow_num_pixels(const fuseflow_ctx *ctx);
+int64_t fuseflow_capacity(const fuseflow_ctx *ctx);
+
+/* Device bytes held by the context (tables, scratch and outputs). */
+int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
+
+/* Static description of a status code. */
+const char *fuseflow_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FUSEFLOW_H */

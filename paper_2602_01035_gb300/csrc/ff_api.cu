@@ -1,0 +1,558 @@
+// ff_api.cu - host side of the C ABI declared in include/fuseflow.h.
+//
+// Create time (host, double precision): relative poses T_ji = T_j T_i^-1 of Eq. 4, the
+// static neighbour table of Sec. II.5(2)b, per-camera ray tables (x - cx)/fx and
+// (y - cy)/fy, all split into float32 hi/lo pairs for the device; device tables are
+// allocated once and reused by every frame.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ff_internal.h"
+
+using namespace ffl;
+
+struct fuseflow_ctx {
+  int device = 0;
+  int n_cams = 0;
+  int k1 = 0;
+  fuseflow_params params{};
+  std::vector<fuseflow_intrinsics> intr;
+  std::vector<fuseflow_extrinsics> extr;
+  std::vector<int32_t> nbr;
+  long long n_px = 0;
+  long long max_cells = 0;
+  unsigned fcap = 0, ccap = 0;
+  RigDev* d_rig = nullptr;
+  float2* d_rays = nullptr;
+  Tables tab{};
+  void* d_tables = nullptr;            // one allocation for every table
+  size_t table_bytes = 0;
+  OutDev out{};
+  void* d_out = nullptr;
+  size_t out_bytes = 0;
+  TraceDev trace{};
+  Geometry geo{};
+  // staging for the host-buffer entry point
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  // stage timing ring
+  bool timing = false;
+  std::vector<cudaEvent_t> events;     // kTimingRing * (FUSEFLOW_N_STAGES + 1)
+  long long timed_frames = 0;
+};
+
+static constexpr int kTimingRing = 1024;
+static constexpr int kEv = FUSEFLOW_N_STAGES + 1;
+
+namespace {
+
+void split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+unsigned next_pow2(unsigned long long v) {
+  unsigned long long p = 1;
+  while (p < v) p <<= 1;
+  return (unsigned)std::min<unsigned long long>(p, 1ull << 31);
+}
+
+// camera centre c = -R^T t and optical axis R^T e_z in world coordinates
+void centre_axis(const fuseflow_extrinsics& e, double c[3], double a[3]) {
+  for (int k = 0; k < 3; ++k) {
+    c[k] = -(e.R[0 + k] * e.t[0] + e.R[3 + k] * e.t[1] + e.R[6 + k] * e.t[2]);
+    a[k] = e.R[6 + k];
+  }
+}
+
+// Sec. II.5(2)b read as a static list: the other cameras by optical-axis angle, then
+// centre distance, then index (values closer than 1e-9 count as equal).
+std::vector<int32_t> neighbour_table(const std::vector<fuseflow_extrinsics>& ex, int k1) {
+  const int n = (int)ex.size();
+  std::vector<int32_t> out((size_t)n * k1);
+  struct Cand { double angle, dist; int j; };
+  for (int i = 0; i < n; ++i) {
+    double ci[3], ai[3];
+    centre_axis(ex[i], ci, ai);
+    const double ni = std::sqrt(ai[0] * ai[0] + ai[1] * ai[1] + ai[2] * ai[2]);
+    std::vector<Cand> cand;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double cj[3], aj[3];
+      centre_axis(ex[j], cj, aj);
+      const double nj = std::sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]);
+      double cs = (ai[0] * aj[0] + ai[1] * aj[1] + ai[2] * aj[2]) / (ni * nj);
+      cs = std::max(-1.0, std::min(1.0, cs));
+      const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+      cand.push_back({std::acos(cs), std::sqrt(dx * dx + dy * dy + dz * dz), j});
+    }
+    // stable insertion order on a tolerance-based key
+    for (size_t a = 1; a < cand.size(); ++a) {
+      Cand v = cand[a];
+      size_t b = a;
+      auto before = [](const Cand& x, const Cand& y) {
+        if (std::fabs(x.angle - y.angle) > 1e-9) return x.angle < y.angle;
+        if (std::fabs(x.dist - y.dist) > 1e-9) return x.dist < y.dist;
+        return x.j < y.j;
+      };
+      while (b > 0 && before(v, cand[b - 1])) { cand[b] = cand[b - 1]; --b; }
+      cand[b] = v;
+    }
+    for (int q = 0; q < k1; ++q) out[(size_t)i * k1 + q] = cand[q].j;
+  }
+  return out;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr, int32_t n,
+             const fuseflow_params* p) {
+  if (!intr || !extr || !p) return FUSEFLOW_ERR_INVALID_ARG;
+  if (n < 1 || n > kMaxCams) return FUSEFLOW_ERR_INVALID_ARG;
+  long long px = 0;
+  for (int i = 0; i < n; ++i) {
+    const fuseflow_intrinsics& k = intr[i];
+    if (!(k.fx > 0) || !(k.fy > 0) || !finite(k.fx) || !finite(k.fy) || !finite(k.cx) ||
+        !finite(k.cy) || k.width < 1 || k.height < 1)
+      return FUSEFLOW_ERR_INVALID_ARG;
+    if ((long long)k.width * k.height > (1ll << 30)) return FUSEFLOW_ERR_INVALID_ARG;
+    px += (long long)k.width * k.height;
+    for (int a = 0; a < 9; ++a) if (!finite(extr[i].R[a])) return FUSEFLOW_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) if (!finite(extr[i].t[a])) return FUSEFLOW_ERR_INVALID_ARG;
+  }
+  if (px >= (1ll << 32) - 1) return FUSEFLOW_ERR_INVALID_ARG;   // pixel index is 32-bit
+  const int K = std::min<int>(p->k_views, n);
+  if (p->k_views < 1 || K - 1 > kMaxK1) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!(p->tau >= 0.0f) || !std::isfinite(p->tau)) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!(p->sigma_m > 0) || !finite(p->sigma_m)) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!(p->coarse_cell_m > 0) || !finite(p->coarse_cell_m)) return FUSEFLOW_ERR_INVALID_ARG;
+  if (p->max_level < 0 || p->max_level > 14 || p->n_min < 1) return FUSEFLOW_ERR_INVALID_ARG;
+  if (p->depth_format != FUSEFLOW_DEPTH_U16 && p->depth_format != FUSEFLOW_DEPTH_F32)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  if (!(p->depth_scale > 0) || !finite(p->depth_scale)) return FUSEFLOW_ERR_INVALID_ARG;
+  if (p->max_cells < 0 || p->max_cells > (1ll << 30)) return FUSEFLOW_ERR_INVALID_ARG;
+  return FUSEFLOW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fuseflow_default_params(fuseflow_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tau = 0.6f;             // Eq. 9
+  p->k_views = 4;
+  p->sigma_m = 0.03;
+  p->coarse_cell_m = 0.32;
+  p->max_level = 4;
+  p->n_min = 32;
+  p->depth_format = FUSEFLOW_DEPTH_U16;
+  p->use_conf = 1;
+  p->depth_scale = 0.001;
+  p->use_consistency = 1;
+  p->max_cells = 0;
+}
+
+const char* fuseflow_status_string(int s) {
+  switch (s) {
+    case FUSEFLOW_OK: return "ok";
+    case FUSEFLOW_ERR_INVALID_ARG: return "invalid argument";
+    case FUSEFLOW_ERR_OUT_OF_MEMORY: return "out of memory";
+    case FUSEFLOW_ERR_CAPACITY: return "capacity exceeded (max_cells or hash table)";
+    case FUSEFLOW_ERR_CUDA: return "CUDA runtime error";
+    case FUSEFLOW_ERR_TIMEOUT: return "device wait timed out";
+    case FUSEFLOW_ERR_INTERNAL: return "internal device check failed";
+    default: return "unknown status";
+  }
+}
+
+void fuseflow_destroy(fuseflow_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->d_rig);
+  cudaFree(ctx->d_rays);
+  cudaFree(ctx->d_tables);
+  cudaFree(ctx->d_out);
+  cudaFree(ctx->d_stage);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr,
+                    int32_t n_cams, const fuseflow_params* params, fuseflow_ctx** out) {
+  if (!out) return FUSEFLOW_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int v = validate(intr, extr, n_cams, params);
+  if (v != FUSEFLOW_OK) return v;
+  fuseflow_ctx* ctx = new (std::nothrow) fuseflow_ctx();
+  if (!ctx) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return FUSEFLOW_ERR_CUDA; }
+  ctx->n_cams = n_cams;
+  ctx->params = *params;
+  ctx->intr.assign(intr, intr + n_cams);
+  ctx->extr.assign(extr, extr + n_cams);
+  const int K = std::min<int>(params->k_views, n_cams);
+  ctx->k1 = K - 1;
+  ctx->nbr = neighbour_table(ctx->extr, ctx->k1);
+  const double unit = params->depth_scale;
+
+  // ---------------------------------------------------------------- rig constants
+  RigDev* rig = new (std::nothrow) RigDev();
+  if (!rig) { delete ctx; return FUSEFLOW_ERR_OUT_OF_MEMORY; }
+  rig->n_cams = n_cams;
+  rig->k1 = ctx->k1;
+  rig->tau = params->tau;
+  rig->use_conf = params->use_conf ? 1 : 0;
+  rig->use_cons = params->use_consistency ? 1 : 0;
+  rig->max_level = params->max_level;
+  rig->n_min = params->n_min;
+  rig->inv_s0u = (float)(unit / params->coarse_cell_m);
+  const double sig_u = params->sigma_m / unit;
+  if (ctx->k1 > 0) split(1.0 / (sig_u * sig_u * ctx->k1), rig->einv_h, rig->einv_l);
+  rig->depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
+  std::vector<float2> rays;
+  long long off = 0;
+  int max_w = 0, max_h = 0;
+  long long max_px = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    const fuseflow_intrinsics& k = intr[i];
+    const fuseflow_extrinsics& e = extr[i];
+    CamDev& c = rig->cam[i];
+    c.W = k.width;
+    c.H = k.height;
+    c.off = off;
+    off += (long long)k.width * k.height;
+    max_w = std::max(max_w, k.width);
+    max_h = std::max(max_h, k.height);
+    max_px = std::max(max_px, (long long)k.width * k.height);
+    c.fx = (float)k.fx; c.fy = (float)k.fy; c.cx = (float)k.cx; c.cy = (float)k.cy;
+    split(k.fx, c.fxh, c.fxl);
+    split(k.fy, c.fyh, c.fyl);
+    split(k.cx, c.cxh, c.cxl);
+    split(k.cy, c.cyh, c.cyl);
+    double cen[3], ax[3];
+    centre_axis(e, cen, ax);
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) c.Rwc[3 * r + q] = (float)e.R[3 * q + r];
+      c.cwc[r] = (float)(cen[r] / unit);
+    }
+    c.ray_x = (int)rays.size();
+    for (int x = 0; x < k.width; ++x) {
+      float2 f;
+      split(((double)x - k.cx) / k.fx, f.x, f.y);
+      rays.push_back(f);
+    }
+    c.ray_y = (int)rays.size();
+    for (int y = 0; y < k.height; ++y) {
+      float2 f;
+      split(((double)y - k.cy) / k.fy, f.x, f.y);
+      rays.push_back(f);
+    }
+    c.pair0 = i * ctx->k1;
+    for (int q = 0; q < ctx->k1; ++q) {
+      const int j = ctx->nbr[(size_t)i * ctx->k1 + q];
+      const fuseflow_extrinsics& ej = extr[j];
+      PairDev& P = rig->pair[c.pair0 + q];
+      P.j = j;
+      double Rji[9], tji[3];
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+          double acc = 0;
+          for (int m = 0; m < 3; ++m) acc += ej.R[3 * r + m] * e.R[3 * s + m];   // R_j R_i^T
+          Rji[3 * r + s] = acc;
+        }
+      for (int r = 0; r < 3; ++r)
+        tji[r] = ej.t[r] - (Rji[3 * r] * e.t[0] + Rji[3 * r + 1] * e.t[1] + Rji[3 * r + 2] * e.t[2]);
+      for (int a = 0; a < 9; ++a) split(Rji[a], P.Rh[a], P.Rl[a]);
+      for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
+    }
+  }
+  rig->n_px = off;
+  ctx->n_px = off;
+  ctx->max_cells = params->max_cells > 0 ? params->max_cells : std::max<long long>(1024, (off + 1) / 2);
+  ctx->fcap = next_pow2((unsigned long long)std::max<long long>(2048, 2 * ctx->max_cells));
+  ctx->ccap = ctx->fcap;
+
+  // ---------------------------------------------------------------- launch geometry
+  ctx->geo.n_cams = n_cams;
+  ctx->geo.depth_f32 = rig->depth_f32;
+  ctx->geo.count_blocks_x = (int)((max_px + 1023) / 1024);
+  int tiles_max = 0;
+  for (int i = 0; i < n_cams; ++i)
+    tiles_max = std::max(tiles_max, ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16));
+  ctx->geo.tiles_max = tiles_max;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  ctx->geo.emit_blocks = std::max(1, sms * 4);
+
+  // ---------------------------------------------------------------- device memory
+  int status = FUSEFLOW_OK;
+  const long long n_words = (off + 31) / 32;
+  const int n_wblocks = (int)((n_words + 1023) / 1024);
+  const int n_bstats = ctx->geo.count_blocks_x * n_cams;
+  size_t o = 0;
+  auto take = [&](size_t bytes, size_t align) { o = align_up(o, align); size_t at = o; o += bytes; return at; };
+  const size_t o_meta = take(sizeof(SlotMeta) * ctx->fcap, 256);
+  const size_t o_acc = take(sizeof(SlotAcc) * ctx->fcap, 256);
+  const size_t o_fused = take(sizeof(unsigned) * ctx->fcap, 256);
+  const size_t o_ckey = take(sizeof(unsigned long long) * ctx->ccap, 256);
+  const size_t o_ccnt = take(sizeof(unsigned) * ctx->ccap, 256);
+  const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
+  const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
+  const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
+  const size_t o_rec = take(sizeof(Rec) * (size_t)off, 256);
+  const size_t o_wpre = take(sizeof(unsigned) * (size_t)n_words, 256);
+  const size_t o_bsum = take(sizeof(unsigned) * (size_t)n_wblocks, 256);
+  ctx->table_bytes = o;
+  size_t po = 0;
+  auto take_out = [&](size_t bytes) { po = align_up(po, 256); size_t at = po; po += bytes; return at; };
+  const size_t q_stats = take_out(sizeof(fuseflow_stats));
+  const size_t q_pos = take_out(sizeof(float) * 3 * (size_t)ctx->max_cells);
+  const size_t q_rgb = take_out(sizeof(float) * 3 * (size_t)ctx->max_cells);
+  const size_t q_w = take_out(sizeof(float) * (size_t)ctx->max_cells);
+  const size_t q_cnt = take_out(sizeof(uint32_t) * (size_t)ctx->max_cells);
+  const size_t q_rep = take_out(sizeof(uint32_t) * (size_t)ctx->max_cells);
+  const size_t q_key = take_out(sizeof(unsigned long long) * (size_t)ctx->max_cells);
+  ctx->out_bytes = po;
+
+  if (cudaMalloc(&ctx->d_rig, sizeof(RigDev)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_rays, sizeof(float2) * rays.size()) != cudaSuccess ||
+      cudaMalloc(&ctx->d_tables, ctx->table_bytes) != cudaSuccess ||
+      cudaMalloc(&ctx->d_out, ctx->out_bytes) != cudaSuccess) {
+    status = FUSEFLOW_ERR_OUT_OF_MEMORY;
+  }
+  if (status == FUSEFLOW_OK) {
+    char* b = static_cast<char*>(ctx->d_tables);
+    Tables& t = ctx->tab;
+    t.meta = reinterpret_cast<SlotMeta*>(b + o_meta);
+    t.acc = reinterpret_cast<SlotAcc*>(b + o_acc);
+    t.fused = reinterpret_cast<unsigned*>(b + o_fused);
+    t.fmask = ctx->fcap - 1;
+    t.ckey = reinterpret_cast<unsigned long long*>(b + o_ckey);
+    t.ccount = reinterpret_cast<unsigned*>(b + o_ccnt);
+    t.cused = reinterpret_cast<unsigned*>(b + o_cused);
+    t.cmask = ctx->ccap - 1;
+    t.cnt = reinterpret_cast<FrameCounters*>(b + o_cnt);
+    t.bitmap = reinterpret_cast<unsigned*>(t.cnt + 1);
+    t.bstats = reinterpret_cast<BlockStats*>(b + o_bst);
+    t.n_bstats = n_bstats;
+    t.rec = reinterpret_cast<Rec*>(b + o_rec);
+    t.wprefix = reinterpret_cast<unsigned*>(b + o_wpre);
+    t.bsum = reinterpret_cast<unsigned*>(b + o_bsum);
+    t.n_words = n_words;
+    t.n_wblocks = n_wblocks;
+    char* q = static_cast<char*>(ctx->d_out);
+    OutDev& od = ctx->out;
+    od.stats = reinterpret_cast<fuseflow_stats*>(q + q_stats);
+    od.pos = reinterpret_cast<float*>(q + q_pos);
+    od.rgb = reinterpret_cast<float*>(q + q_rgb);
+    od.weight = reinterpret_cast<float*>(q + q_w);
+    od.count = reinterpret_cast<uint32_t*>(q + q_cnt);
+    od.rep = reinterpret_cast<uint32_t*>(q + q_rep);
+    od.key = reinterpret_cast<unsigned long long*>(q + q_key);
+    od.max_cells = ctx->max_cells;
+    od.s0_m = params->coarse_cell_m;
+    od.unit_m = unit;
+    if (cudaMemcpy(ctx->d_rig, rig, sizeof(RigDev), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_rays, rays.data(), sizeof(float2) * rays.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ctx->d_tables, 0, ctx->table_bytes) != cudaSuccess ||
+        cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
+        launch_init_tables(t, ctx->fcap, ctx->ccap, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      status = FUSEFLOW_ERR_CUDA;
+  }
+  delete rig;
+  if (status != FUSEFLOW_OK) {
+    cudaGetLastError();
+    fuseflow_destroy(ctx);
+    return status;
+  }
+  *out = ctx;
+  return FUSEFLOW_OK;
+}
+
+static FramePtrs frame_ptrs(const fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                            const uint8_t* const* rgb, int* ok) {
+  FramePtrs fp{};
+  *ok = depth && conf && rgb;
+  for (int i = 0; *ok && i < ctx->n_cams; ++i) {
+    if (!depth[i] || !conf[i] || !rgb[i]) { *ok = 0; break; }
+    fp.depth[i] = depth[i];
+    fp.conf[i] = conf[i];
+    fp.rgb[i] = rgb[i];
+  }
+  return fp;
+}
+
+static void fill_cloud(const fuseflow_ctx* ctx, fuseflow_cloud* out) {
+  out->stats = ctx->out.stats;
+  out->pos = ctx->out.pos;
+  out->rgb = ctx->out.rgb;
+  out->weight = ctx->out.weight;
+  out->count = ctx->out.count;
+  out->rep = ctx->out.rep;
+  out->key = reinterpret_cast<uint64_t*>(ctx->out.key);
+  out->capacity = ctx->max_cells;
+}
+
+int fuseflow_fuse_frame(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                        const uint8_t* const* rgb, fuseflow_cloud* out, void* stream) {
+  if (!ctx) return FUSEFLOW_ERR_INVALID_ARG;
+  int ok = 0;
+  const FramePtrs fp = frame_ptrs(ctx, depth, conf, rgb, &ok);
+  if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
+  cudaEvent_t* ev = nullptr;
+  if (ctx->timing) {
+    ev = &ctx->events[(size_t)(ctx->timed_frames % kTimingRing) * kEv];
+    ++ctx->timed_frames;
+  }
+  const cudaError_t e = launch_frame(ctx->d_rig, ctx->d_rays, fp, ctx->tab, ctx->trace, ctx->out,
+                                     ctx->geo, static_cast<cudaStream_t>(stream), ev);
+  if (e != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+  if (out) fill_cloud(ctx, out);
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_read_stats(fuseflow_ctx* ctx, fuseflow_stats* host_stats, void* stream) {
+  if (!ctx || !host_stats) return FUSEFLOW_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(host_stats, ctx->out.stats, sizeof(fuseflow_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+  const unsigned err = (unsigned)host_stats->error;
+  if (err & (kErrFineFull | kErrCoarseFull | kErrCells)) return FUSEFLOW_ERR_CAPACITY;
+  if (err & kErrCoarseMiss) return FUSEFLOW_ERR_INTERNAL;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_fuse_frame_host(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                             const uint8_t* const* rgb, float* pos, float* rgb_out, float* weight,
+                             uint32_t* count, uint32_t* rep, uint64_t* key, fuseflow_stats* host_stats,
+                             void* stream) {
+  if (!ctx || !depth || !conf || !rgb || !host_stats) return FUSEFLOW_ERR_INVALID_ARG;
+  const size_t dsz = ctx->params.depth_format == FUSEFLOW_DEPTH_F32 ? 4 : 2;
+  if (!ctx->d_stage) {
+    ctx->stage_bytes = 0;
+    for (int i = 0; i < ctx->n_cams; ++i) {
+      const size_t px = (size_t)ctx->intr[i].width * ctx->intr[i].height;
+      ctx->stage_bytes += align_up(px * dsz, 256) + align_up(px * 4, 256) + align_up(px * 3, 256);
+    }
+    if (cudaMalloc(&ctx->d_stage, ctx->stage_bytes) != cudaSuccess) {
+      ctx->d_stage = nullptr;
+      return FUSEFLOW_ERR_OUT_OF_MEMORY;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const void*> dp(ctx->n_cams);
+  std::vector<const float*> cp(ctx->n_cams);
+  std::vector<const uint8_t*> rp(ctx->n_cams);
+  char* b = static_cast<char*>(ctx->d_stage);
+  size_t o = 0;
+  for (int i = 0; i < ctx->n_cams; ++i) {
+    if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
+    const size_t px = (size_t)ctx->intr[i].width * ctx->intr[i].height;
+    char* d = b + o; o += align_up(px * dsz, 256);
+    char* c = b + o; o += align_up(px * 4, 256);
+    char* r = b + o; o += align_up(px * 3, 256);
+    if (cudaMemcpyAsync(d, depth[i], px * dsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c, conf[i], px * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(r, rgb[i], px * 3, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+    dp[i] = d;
+    cp[i] = reinterpret_cast<const float*>(c);
+    rp[i] = reinterpret_cast<const uint8_t*>(r);
+  }
+  fuseflow_cloud cl;
+  int st = fuseflow_fuse_frame(ctx, dp.data(), cp.data(), rp.data(), &cl, stream);
+  if (st != FUSEFLOW_OK) return st;
+  st = fuseflow_read_stats(ctx, host_stats, stream);
+  const size_t n = (size_t)std::max<int64_t>(0, host_stats->n_cells);
+  if (n) {
+    struct { void* dst; const void* src; size_t sz; } cp_list[6] = {
+        {pos, cl.pos, 12}, {rgb_out, cl.rgb, 12}, {weight, cl.weight, 4},
+        {count, cl.count, 4}, {rep, cl.rep, 4}, {key, cl.key, 8}};
+    for (auto& c : cp_list)
+      if (c.dst && cudaMemcpyAsync(c.dst, c.src, c.sz * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FUSEFLOW_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+  }
+  return st;
+}
+
+int fuseflow_set_trace(fuseflow_ctx* ctx, const fuseflow_trace* trace) {
+  if (!ctx) return FUSEFLOW_ERR_INVALID_ARG;
+  ctx->trace = TraceDev{};
+  if (trace) {
+    ctx->trace.pw = trace->pw;
+    ctx->trace.omega = trace->omega;
+    ctx->trace.e = trace->e;
+    ctx->trace.nview = trace->nview;
+    ctx->trace.key = reinterpret_cast<unsigned long long*>(trace->key);
+  }
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_get_neighbours(const fuseflow_ctx* ctx, int32_t* out, int32_t* k_minus_1) {
+  if (!ctx || !k_minus_1) return FUSEFLOW_ERR_INVALID_ARG;
+  *k_minus_1 = ctx->k1;
+  if (out && !ctx->nbr.empty()) std::memcpy(out, ctx->nbr.data(), sizeof(int32_t) * ctx->nbr.size());
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_enable_stage_timing(fuseflow_ctx* ctx, int enable) {
+  if (!ctx) return FUSEFLOW_ERR_INVALID_ARG;
+  if (enable && ctx->events.empty()) {
+    ctx->events.resize((size_t)kTimingRing * kEv);
+    for (auto& e : ctx->events)
+      if (cudaEventCreate(&e) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+  }
+  ctx->timing = enable != 0;
+  ctx->timed_frames = 0;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_read_stage_times(fuseflow_ctx* ctx, double* ms, int64_t* n_frames) {
+  if (!ctx || !ms || !n_frames) return FUSEFLOW_ERR_INVALID_ARG;
+  for (int k = 0; k < FUSEFLOW_N_STAGES; ++k) ms[k] = 0.0;
+  const long long n = std::min<long long>(ctx->timed_frames, kTimingRing);
+  *n_frames = n;
+  if (n == 0) return FUSEFLOW_OK;
+  const long long last = (ctx->timed_frames - 1) % kTimingRing;
+  if (cudaEventSynchronize(ctx->events[(size_t)last * kEv + kEv - 1]) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+  for (long long f = 0; f < n; ++f) {
+    const cudaEvent_t* ev = &ctx->events[(size_t)f * kEv];
+    for (int k = 0; k < FUSEFLOW_N_STAGES; ++k) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+      ms[k] += t;
+    }
+  }
+  ctx->timed_frames = 0;
+  return FUSEFLOW_OK;
+}
+
+const char* fuseflow_stage_name(int stage) {
+  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "accumulate", "scan",
+                                                 "emit"};
+  return (stage >= 0 && stage < FUSEFLOW_N_STAGES) ? names[stage] : "unknown";
+}
+
+int64_t fuseflow_num_pixels(const fuseflow_ctx* ctx) { return ctx ? ctx->n_px : 0; }
+int64_t fuseflow_capacity(const fuseflow_ctx* ctx) { return ctx ? ctx->max_cells : 0; }
+int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
+  return ctx ? (int64_t)(ctx->table_bytes + ctx->out_bytes + ctx->stage_bytes + sizeof(RigDev)) : 0;
+}
+
+}  // extern "C"

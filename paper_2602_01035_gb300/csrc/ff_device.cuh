@@ -1,0 +1,219 @@
+// ff_device.cuh - device data layout and per-pixel arithmetic of the sm_103a fusion path.
+//
+// Geometry is carried in "depth units" (metres per unit = depth_scale), so that the depth
+// sample z of a pixel is exact in float32 (uint16 codes and float32 samples both are).
+// World points, cell keys and the projection that selects a pixel are float32; the 3D
+// residual of Eq. 6 is evaluated in double-float ("ff", an unevaluated hi + lo pair of
+// float32) so that the joint weight of Eq. 10 keeps ~1e-7 relative accuracy although the
+// residual is a difference of two metre-scale vectors.  The error-free transformations are
+// Knuth's TwoSum, Dekker's Fast2Sum and the FMA TwoProduct, combined as in the compensated
+// dot product of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6), 2005).
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+namespace ffl {
+
+constexpr int kMaxCams = 64;
+constexpr int kMaxK1 = 8;
+constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr uint32_t kSlotNone = 0xffffffffu;
+constexpr int kFixShift = 36;            // per-cell fixed point: largest member weight ~ 2^36
+constexpr int kKeyBias = 1 << 19;        // cell index range [-2^19, 2^19) per axis
+constexpr float kTieBandPx = 4e-3f;      // float32 projection error bound (pixels), generous
+constexpr float kZGuard = 1.0f;          // |a_z| below one depth unit: use the ff value
+
+// error bits of FrameCounters::error
+constexpr unsigned kErrFineFull = 1u;    // fine hash table could not take a key
+constexpr unsigned kErrCoarseFull = 2u;  // coarse hash table could not take a key
+constexpr unsigned kErrCells = 4u;       // more cells than the output capacity
+constexpr unsigned kErrCoarseMiss = 8u;  // a point's coarse cell was not found (internal)
+
+struct CamDev {
+  int W, H;
+  long long off;                 // global index of pixel (0, 0)
+  float fx, fy, cx, cy;          // float32 intrinsics (projection into this camera)
+  float fxh, fxl, fyh, fyl;      // ff intrinsics for exact half-pixel decisions
+  float cxh, cxl, cyh, cyl;
+  float Rwc[9];                  // world-from-camera rotation R^T, row-major
+  float cwc[3];                  // camera centre (depth units)
+  int ray_x, ray_y;              // offsets of this camera's ray tables
+  int pair0;                     // first neighbour pair of this camera
+  int pad;
+};
+
+struct PairDev {                 // camera i -> neighbour j: a = R_ji p_c + t_ji
+  float Rh[9], Rl[9];            // R_ji = R_j R_i^T as ff
+  float th[3], tl[3];            // t_ji = t_j - R_ji t_i as ff (depth units)
+  int j;
+  int pad[3];
+};
+
+struct RigDev {
+  int n_cams, k1;                // k1 = K - 1 neighbours per camera
+  float tau;                     // Eq. 9 gate
+  int use_conf, use_cons;
+  int max_level, n_min;
+  float inv_s0u;                 // 1 / s0 in 1 / depth units
+  float einv_h, einv_l;          // 1 / (sigma_u^2 (K-1)) as ff
+  int depth_f32;
+  int pad;
+  long long n_px;
+  CamDev cam[kMaxCams];
+  PairDev pair[kMaxCams * kMaxK1];
+};
+
+// One entry per fine cell (hash slot); cleared by the emit step after use.
+struct __align__(32) SlotMeta {
+  unsigned long long key;        // cell key or kKeyEmpty
+  unsigned long long rep;        // max of (float bits of C) << 32 | ~g
+  int mmin;                      // smallest binary exponent m of a member weight
+  unsigned count;                // members
+  unsigned long long pad;
+};
+
+struct __align__(64) SlotAcc {   // exact integer sums in units of 2^-(kFixShift + mmin)
+  unsigned long long w, x, y, z, r, g, b, pad;
+};
+
+struct Rec {                     // per pixel, written by the assign step
+  uint32_t slot;                 // fine slot or kSlotNone
+  float mu;                      // weight mantissa: omega = mu * 2^-m
+  int m;
+};
+
+struct FrameCounters {
+  unsigned n_cells, n_coarse;
+  unsigned error;
+  unsigned pad;
+};
+
+struct BlockStats {              // per block of the coarse-count step
+  unsigned n_valid, n_gated, n_oor, pad;
+  unsigned bmin[3], bmax[3];     // ordered-integer encodings
+  unsigned pad2[2];
+};
+
+// ----------------------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned ordered(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float from_ordered(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+#else
+  unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+#endif
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+  k ^= k >> 31;
+  k *= 0x7fb5d329728ea185ull;
+  k ^= k >> 27;
+  k *= 0x81dadef4bc2dd44dull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int l, int kx, int ky, int kz) {
+  return ((unsigned long long)l << 60) | ((unsigned long long)(kx + kKeyBias) << 40) |
+         ((unsigned long long)(ky + kKeyBias) << 20) | (unsigned long long)(kz + kKeyBias);
+}
+
+// --------------------------------------------------------------------------- double-float
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// Row k of an affine map in ff: o = R[k,:] . (px, py, z) + t[k], with px, py ff and z exact.
+__device__ __forceinline__ void ff_affine_row(const float* Rh, const float* Rl, float th, float tl,
+                                              float pxh, float pxl, float pyh, float pyl, float z,
+                                              float& oh, float& ol) {
+  float p1, e1, p2, e2, p3, e3;
+  two_prod(Rh[0], pxh, p1, e1);
+  e1 = __fmaf_rn(Rh[0], pxl, e1);
+  e1 = __fmaf_rn(Rl[0], pxh, e1);
+  two_prod(Rh[1], pyh, p2, e2);
+  e2 = __fmaf_rn(Rh[1], pyl, e2);
+  e2 = __fmaf_rn(Rl[1], pyh, e2);
+  two_prod(Rh[2], z, p3, e3);
+  e3 = __fmaf_rn(Rl[2], z, e3);
+  float s, q1, q2, q3;
+  two_sum(p1, p2, s, q1);
+  two_sum(s, p3, s, q2);
+  two_sum(s, th, s, q3);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, q1)),
+                             __fadd_rn(__fadd_rn(q2, q3), tl));
+  fast_two_sum(s, lo, oh, ol);
+}
+
+// --------------------------------------------------------------------------- depth decode
+template <typename DT> struct Depth;
+template <> struct Depth<uint16_t> {
+  static __device__ __forceinline__ bool valid(uint16_t d) { return d != 0; }
+  static __device__ __forceinline__ float z(uint16_t d) { return (float)d; }
+};
+template <> struct Depth<float> {
+  static __device__ __forceinline__ bool valid(float d) { return d > 0.0f && d < __int_as_float(0x7f800000); }
+  static __device__ __forceinline__ float z(float d) { return d; }
+};
+
+// Eq. 8 in float32: world point (depth units) of pixel ray (rx, ry, 1) at z-depth z.
+// Every step uses the same rounding-explicit sequence so all kernels agree bit for bit.
+__device__ __forceinline__ void world_point(const CamDev& c, float z, float rx, float ry,
+                                            float P[3]) {
+  const float px = __fmul_rn(z, rx), py = __fmul_rn(z, ry);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    P[k] = __fmaf_rn(c.Rwc[3 * k + 0], px,
+                     __fmaf_rn(c.Rwc[3 * k + 1], py, __fmaf_rn(c.Rwc[3 * k + 2], z, c.cwc[k])));
+}
+
+// Sec. II.5(1): coarse-grid coordinate r = P / s0 and the range test at the finest level.
+__device__ __forceinline__ bool grid_coords(const RigDev& rig, const float P[3], float r[3]) {
+  bool ok = true;
+  const float lim = (float)kKeyBias;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r[k] = __fmul_rn(P[k], rig.inv_s0u);
+    const float f = floorf(ldexpf(r[k], rig.max_level));
+    ok = ok && (f >= -lim) && (f < lim);
+  }
+  return ok;
+}
+
+__device__ __forceinline__ unsigned long long coarse_key(const float r[3]) {
+  return pack_key(0, (int)floorf(r[0]), (int)floorf(r[1]), (int)floorf(r[2]));
+}
+
+// Sec. II.5(1)d: level of a coarse cell holding n_c points: largest l <= Lmax with
+// n_c >= n_min 4^l, else 0.
+__device__ __forceinline__ int level_for(unsigned n_c, int n_min, int max_level) {
+  int l = 0;
+  for (int c = 1; c <= max_level; ++c)
+    if ((unsigned long long)n_c >= ((unsigned long long)n_min << (2 * c))) l = c;
+  return l;
+}
+
+__device__ __forceinline__ unsigned long long fine_key(const float r[3], int l) {
+  return pack_key(l, (int)floorf(ldexpf(r[0], l)), (int)floorf(ldexpf(r[1], l)),
+                  (int)floorf(ldexpf(r[2], l)));
+}
+
+}  // namespace ffl

@@ -1,0 +1,73 @@
+// ff_internal.h - host <-> kernel interface of the fusion path (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fuseflow.h"
+#include "ff_device.cuh"
+
+namespace ffl {
+
+struct FramePtrs {               // one frame's caller-owned device images, per camera
+  const void* depth[kMaxCams];
+  const float* conf[kMaxCams];
+  const uint8_t* rgb[kMaxCams];
+};
+
+struct Tables {                  // context-owned device scratch
+  SlotMeta* meta;                // fine hash table, fcap entries
+  SlotAcc* acc;
+  unsigned* fused;               // used fine slots, in insertion order
+  unsigned fmask;                // fcap - 1
+  unsigned long long* ckey;      // coarse hash table, ccap entries
+  unsigned* ccount;
+  unsigned* cused;
+  unsigned cmask;
+  FrameCounters* cnt;
+  BlockStats* bstats;            // one per block of the coarse-count step
+  int n_bstats;
+  Rec* rec;                      // one per pixel
+  unsigned* bitmap;              // representative bitmap, one bit per pixel
+  unsigned* wprefix;             // per-word exclusive prefix within its 1024-word block
+  unsigned* bsum;                // per 1024-word block: exclusive prefix after the scan
+  long long n_words;
+  int n_wblocks;
+};
+
+struct TraceDev {
+  float* pw;
+  float* omega;
+  float* e;
+  int* nview;
+  unsigned long long* key;
+};
+
+struct OutDev {
+  fuseflow_stats* stats;
+  float* pos;
+  float* rgb;
+  float* weight;
+  uint32_t* count;
+  uint32_t* rep;
+  unsigned long long* key;
+  long long max_cells;
+  double s0_m;                   // coarse edge, metres
+  double unit_m;                 // metres per depth unit
+};
+
+struct Geometry {
+  int n_cams;
+  int depth_f32;
+  int count_blocks_x;            // blocks per camera of the coarse-count step (max over cams)
+  int tiles_max;                 // 32x16 tiles per camera (max over cams)
+  int emit_blocks;
+};
+
+cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cudaStream_t s);
+// ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages
+cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp,
+                         const Tables& t, const TraceDev& tr, const OutDev& out,
+                         const Geometry& geo, cudaStream_t s, cudaEvent_t* ev);
+
+}  // namespace ffl

@@ -1,0 +1,321 @@
+"""Python binding of the C ABI in ``include/fuseflow.h`` (ctypes, argument marshalling only).
+
+Every function here carries the name of the C entry point it calls.  Device memory and
+streams come from PyTorch; all arithmetic of the fusion path runs in ``libfuseflow.so``.
+There is no fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+FUSEFLOW_OK = 0
+FUSEFLOW_ERR_INVALID_ARG = 1
+FUSEFLOW_ERR_OUT_OF_MEMORY = 2
+FUSEFLOW_ERR_CAPACITY = 3
+FUSEFLOW_ERR_CUDA = 4
+FUSEFLOW_ERR_TIMEOUT = 5
+FUSEFLOW_ERR_INTERNAL = 6
+FUSEFLOW_DEPTH_U16 = 0
+FUSEFLOW_DEPTH_F32 = 1
+KEY_NONE = 0xFFFFFFFFFFFFFFFF
+
+
+class fuseflow_intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class fuseflow_extrinsics(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class fuseflow_params(C.Structure):
+    _fields_ = [("tau", C.c_float), ("k_views", C.c_int32), ("sigma_m", C.c_double),
+                ("coarse_cell_m", C.c_double), ("max_level", C.c_int32), ("n_min", C.c_int32),
+                ("depth_format", C.c_int32), ("use_conf", C.c_int32), ("depth_scale", C.c_double),
+                ("use_consistency", C.c_int32), ("reserved0", C.c_int32), ("max_cells", C.c_int64)]
+
+
+class fuseflow_stats(C.Structure):
+    _fields_ = [("n_valid", C.c_int64), ("n_gated", C.c_int64), ("n_out_of_range", C.c_int64),
+                ("n_cells", C.c_int64), ("bbox", C.c_float * 6), ("error", C.c_int32),
+                ("n_coarse", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"n_valid": self.n_valid, "n_gated": self.n_gated,
+                "n_out_of_range": self.n_out_of_range, "n_cells": self.n_cells,
+                "bbox": list(self.bbox), "error": self.error, "n_coarse": self.n_coarse}
+
+
+class fuseflow_cloud(C.Structure):
+    _fields_ = [("stats", C.c_void_p), ("pos", C.c_void_p), ("rgb", C.c_void_p),
+                ("weight", C.c_void_p), ("count", C.c_void_p), ("rep", C.c_void_p),
+                ("key", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class fuseflow_trace(C.Structure):
+    _fields_ = [("pw", C.c_void_p), ("omega", C.c_void_p), ("e", C.c_void_p),
+                ("nview", C.c_void_p), ("key", C.c_void_p)]
+
+
+EXPORTS = {
+    "fuseflow_default_params": (None, [C.POINTER(fuseflow_params)]),
+    "fuseflow_create": (C.c_int, [C.POINTER(fuseflow_intrinsics), C.POINTER(fuseflow_extrinsics),
+                                  C.c_int32, C.POINTER(fuseflow_params), C.POINTER(C.c_void_p)]),
+    "fuseflow_destroy": (None, [C.c_void_p]),
+    "fuseflow_fuse_frame": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(fuseflow_cloud), C.c_void_p]),
+    "fuseflow_read_stats": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_stats), C.c_void_p]),
+    "fuseflow_fuse_frame_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.POINTER(fuseflow_stats), C.c_void_p]),
+    "fuseflow_set_trace": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_trace)]),
+    "fuseflow_get_neighbours": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "fuseflow_num_pixels": (C.c_int64, [C.c_void_p]),
+    "fuseflow_capacity": (C.c_int64, [C.c_void_p]),
+    "fuseflow_device_bytes": (C.c_int64, [C.c_void_p]),
+    "fuseflow_status_string": (C.c_char_p, [C.c_int]),
+    "fuseflow_enable_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "fuseflow_read_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "fuseflow_stage_name": (C.c_char_p, [C.c_int]),
+}
+FUSEFLOW_N_STAGES = 6
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfuseflow.so (building it in-tree when stale); raises if it cannot."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libfuseflow.so not found at {_build.LIB}; run build()")
+        lib = C.CDLL(_build.LIB)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class FuseFlowError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().fuseflow_status_string(status).decode()
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != FUSEFLOW_OK:
+        raise FuseFlowError(status, where)
+
+
+# --------------------------------------------------------------------------- marshalling
+def fuseflow_default_params(**overrides) -> fuseflow_params:
+    p = fuseflow_params()
+    load().fuseflow_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def rig_arrays(rig):
+    """(intrinsics[], extrinsics[]) ctypes arrays from a rig of pinhole cameras."""
+    n = len(rig.cameras)
+    intr = (fuseflow_intrinsics * n)()
+    extr = (fuseflow_extrinsics * n)()
+    for i, c in enumerate(rig.cameras):
+        intr[i] = fuseflow_intrinsics(c.fx, c.fy, c.cx, c.cy, c.width, c.height)
+        extr[i].R[:] = [float(v) for v in np.asarray(c.R, dtype=np.float64).ravel()]
+        extr[i].t[:] = [float(v) for v in np.asarray(c.t, dtype=np.float64).ravel()]
+    return intr, extr
+
+
+def fuseflow_create(intr, extr, n_cams: int, params: fuseflow_params) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(load().fuseflow_create(intr, extr, n_cams, C.byref(params), C.byref(ctx)),
+           "fuseflow_create")
+    return ctx
+
+
+def fuseflow_destroy(ctx) -> None:
+    load().fuseflow_destroy(ctx)
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    arr = (C.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = int(p)
+    return arr
+
+
+def fuseflow_fuse_frame(ctx, depth_ptrs, conf_ptrs, rgb_ptrs, stream: int = 0) -> fuseflow_cloud:
+    cloud = fuseflow_cloud()
+    _check(load().fuseflow_fuse_frame(ctx, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                      _ptr_array(rgb_ptrs), C.byref(cloud), C.c_void_p(stream)),
+           "fuseflow_fuse_frame")
+    return cloud
+
+
+def fuseflow_read_stats(ctx, stream: int = 0, check: bool = True):
+    st = fuseflow_stats()
+    status = load().fuseflow_read_stats(ctx, C.byref(st), C.c_void_p(stream))
+    if check:
+        _check(status, "fuseflow_read_stats")
+    return status, st
+
+
+def fuseflow_fuse_frame_host(ctx, depth_ptrs, conf_ptrs, rgb_ptrs, pos, rgb_out, weight, count,
+                             rep, key, stream: int = 0):
+    st = fuseflow_stats()
+    status = load().fuseflow_fuse_frame_host(
+        ctx, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs), _ptr_array(rgb_ptrs),
+        C.c_void_p(pos), C.c_void_p(rgb_out), C.c_void_p(weight), C.c_void_p(count),
+        C.c_void_p(rep), C.c_void_p(key), C.byref(st), C.c_void_p(stream))
+    return status, st
+
+
+def fuseflow_set_trace(ctx, pw=0, omega=0, e=0, nview=0, key=0, clear: bool = False):
+    if clear:
+        _check(load().fuseflow_set_trace(ctx, None), "fuseflow_set_trace")
+        return
+    tr = fuseflow_trace(pw, omega, e, nview, key)
+    _check(load().fuseflow_set_trace(ctx, C.byref(tr)), "fuseflow_set_trace")
+
+
+def fuseflow_get_neighbours(ctx, n_cams: int) -> np.ndarray:
+    k1 = C.c_int32()
+    _check(load().fuseflow_get_neighbours(ctx, None, C.byref(k1)), "fuseflow_get_neighbours")
+    out = np.zeros(max(n_cams * k1.value, 1), dtype=np.int32)
+    _check(load().fuseflow_get_neighbours(ctx, out.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          C.byref(k1)), "fuseflow_get_neighbours")
+    return out[:n_cams * k1.value].reshape(n_cams, k1.value)
+
+
+def fuseflow_num_pixels(ctx) -> int:
+    return int(load().fuseflow_num_pixels(ctx))
+
+
+def fuseflow_capacity(ctx) -> int:
+    return int(load().fuseflow_capacity(ctx))
+
+
+def fuseflow_device_bytes(ctx) -> int:
+    return int(load().fuseflow_device_bytes(ctx))
+
+
+def fuseflow_enable_stage_timing(ctx, enable: bool) -> None:
+    _check(load().fuseflow_enable_stage_timing(ctx, 1 if enable else 0),
+           "fuseflow_enable_stage_timing")
+
+
+def fuseflow_read_stage_times(ctx):
+    """(dict stage name -> summed ms, number of frames) since timing was enabled."""
+    ms = (C.c_double * FUSEFLOW_N_STAGES)()
+    n = C.c_int64()
+    _check(load().fuseflow_read_stage_times(ctx, ms, C.byref(n)), "fuseflow_read_stage_times")
+    return {fuseflow_stage_name(k): ms[k] for k in range(FUSEFLOW_N_STAGES)}, n.value
+
+
+def fuseflow_stage_name(stage: int) -> str:
+    return load().fuseflow_stage_name(stage).decode()
+
+
+def fuseflow_status_string(status: int) -> str:
+    return load().fuseflow_status_string(status).decode()
+
+
+# --------------------------------------------------------------------------- torch helpers
+class _CudaArray:
+    """Zero-copy view of a context-owned device array (``__cuda_array_interface__``)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str):
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+class FuseFlow:
+    """One context per rig: ``fuse(depth, conf, rgb)`` takes lists of CUDA tensors."""
+
+    def __init__(self, rig, **params):
+        self.rig = rig
+        fmt = FUSEFLOW_DEPTH_F32 if rig.depth_format == "f32" else FUSEFLOW_DEPTH_U16
+        p = fuseflow_default_params(depth_format=fmt, depth_scale=float(rig.depth_scale))
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.params = p
+        self.intr, self.extr = rig_arrays(rig)
+        self.ctx = fuseflow_create(self.intr, self.extr, len(rig.cameras), p)
+        self.n_pixels = fuseflow_num_pixels(self.ctx)
+        self.capacity = fuseflow_capacity(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            fuseflow_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def neighbours(self) -> np.ndarray:
+        return fuseflow_get_neighbours(self.ctx, len(self.rig.cameras))
+
+    def fuse_ptrs(self, depth_ptrs, conf_ptrs, rgb_ptrs, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_fuse_frame(self.ctx, depth_ptrs, conf_ptrs, rgb_ptrs, stream)
+
+    def fuse(self, depth, conf, rgb, stream: Optional[int] = None):
+        for t in list(depth) + list(conf) + list(rgb):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("inputs must be contiguous CUDA tensors")
+        return self.fuse_ptrs([t.data_ptr() for t in depth], [t.data_ptr() for t in conf],
+                              [t.data_ptr() for t in rgb], stream)
+
+    def stats(self, stream: Optional[int] = None, check: bool = True):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_read_stats(self.ctx, stream, check)
+
+    def cloud_tensors(self, cloud: fuseflow_cloud, n: int) -> dict:
+        """Zero-copy torch views of the first ``n`` cells of a fused cloud (count, rep and key
+        are exposed as signed integers of the same width; view them as unsigned)."""
+        return {"pos": device_view(cloud.pos, (n, 3), "<f4"),
+                "rgb": device_view(cloud.rgb, (n, 3), "<f4"),
+                "weight": device_view(cloud.weight, (n,), "<f4"),
+                "count": device_view(cloud.count, (n,), "<i4"),
+                "rep": device_view(cloud.rep, (n,), "<i4"),
+                "key": device_view(cloud.key, (n,), "<i8")}
+
+    def set_trace(self, **arrays):
+        fuseflow_set_trace(self.ctx, **{k: (v.data_ptr() if v is not None else 0)
+                                        for k, v in arrays.items()})
+
+    def clear_trace(self):
+        fuseflow_set_trace(self.ctx, clear=True)

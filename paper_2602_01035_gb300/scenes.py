@@ -31,7 +31,8 @@ seed 0); the scene layout of config ``c`` uses seed ``1000*c + 999``.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+import warnings
+from dataclasses import dataclass
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -291,31 +292,37 @@ def _colour_hash(pts: np.ndarray) -> np.ndarray:
     return rgb.astype(np.uint8)
 
 
-def _flying_pixels(z_true, z_noisy, frac, rng):
-    """Replace ``frac`` of the pixels, drawn among depth-edge pixels, by a fg/bg blend."""
-    H, W = z_true.shape
+def _depth_edges(z_true):
+    """Depth-edge pixels (4-neighbourhood range above 0.1 m) with their fg/bg depths."""
     zt = np.where(z_true > 0, z_true, np.nan)
     pad = np.pad(zt, 1, constant_values=np.nan)
     nb = np.stack([pad[1:-1, :-2], pad[1:-1, 2:], pad[:-2, 1:-1], pad[2:, 1:-1], zt])
-    with np.errstate(invalid="ignore"), np.testing.suppress_warnings() as sup:
-        sup.filter(RuntimeWarning)
+    with np.errstate(invalid="ignore"), warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)
         zmin = np.nanmin(nb, axis=0)
         zmax = np.nanmax(nb, axis=0)
     edge = np.isfinite(zmin) & (zmax - zmin > 0.1)
     idx = np.flatnonzero(edge)
+    return idx, zmin.ravel()[idx], zmax.ravel()[idx]
+
+
+def _flying_pixels(edges, z_noisy, frac, rng):
+    """Replace ``frac`` of the pixels, drawn among depth-edge pixels, by a fg/bg blend."""
+    idx, zmin, zmax = edges
+    H, W = z_noisy.shape
     n_fly = min(idx.size, int(round(frac * H * W)))
     if n_fly == 0:
         return z_noisy
-    pick = rng.choice(idx, size=n_fly, replace=False)
+    pick = rng.choice(idx.size, size=n_fly, replace=False)
     mix = rng.uniform(0.0, 1.0, size=n_fly)
     out = z_noisy.copy().ravel()
-    out[pick] = zmin.ravel()[pick] + mix * (zmax.ravel()[pick] - zmin.ravel()[pick])
+    out[idx[pick]] = zmin[pick] + mix * (zmax[pick] - zmin[pick])
     return out.reshape(H, W)
 
 
 def render_frame(rig: Rig, prims, seed: int, noise_k: float = 0.0015, zero_frac: float = 0.0,
                  flying_frac: float = 0.0, conf_jitter: float = 0.05, keep_truth: bool = False,
-                 noiseless: bool = False) -> Frame:
+                 noiseless: bool = False, cache: Optional[dict] = None) -> Frame:
     """Render depth/confidence/colour for every camera of ``rig``.
 
     * depth: z-depth + N(0, (noise_k z^2)^2), encoded as uint16 (rounded depth units,
@@ -324,25 +331,34 @@ def render_frame(rig: Rig, prims, seed: int, noise_k: float = 0.0015, zero_frac:
       with cos(grazing) = sqrt(1 - (n . r)^2) for surface normal n and unit view ray r:
       frontal views give about 1, grazing views about 0.5.
     * colour: hash of the 1 cm lattice cell of the true surface point.
+
+    ``cache`` (a dict) keeps the ray-cast of each camera between frames of a static scene.
     """
     rng = np.random.default_rng(seed)
     depth, conf, rgb, ztrue, sids = [], [], [], [], []
-    for cam in rig.cameras:
-        z, n, pts, sid, d = ray_cast(cam, prims)
+    for ci, cam in enumerate(rig.cameras):
+        if cache is not None and ci in cache:
+            z, n, pts, sid, d, cos_graze, col, edges = cache[ci]
+        else:
+            z, n, pts, sid, d = ray_cast(cam, prims)
+            rhat = d / np.linalg.norm(d, axis=-1, keepdims=True)
+            ndotr = np.einsum("...k,...k->...", n, rhat)
+            cos_graze = np.sqrt(np.clip(1.0 - ndotr * ndotr, 0.0, 1.0))
+            col = np.where((z > 0)[..., None], _colour_hash(pts), 0).astype(np.uint8)
+            edges = _depth_edges(z) if flying_frac > 0 else None
+            if cache is not None:
+                cache[ci] = (z, n, pts, sid, d, cos_graze, col, edges)
         hit = z > 0
         if noiseless:
             zn = z.copy()
         else:
             zn = z + rng.normal(0.0, 1.0, size=z.shape) * noise_k * z * z
         if flying_frac > 0:
-            zn = _flying_pixels(z, zn, flying_frac, rng)
+            zn = _flying_pixels(edges if edges is not None else _depth_edges(z), zn, flying_frac, rng)
         zn = np.where(hit & (zn > 0), zn, 0.0)
         if zero_frac > 0:
             kill = rng.random(z.shape) < zero_frac
             zn = np.where(kill, 0.0, zn)
-        rhat = d / np.linalg.norm(d, axis=-1, keepdims=True)
-        ndotr = np.einsum("...k,...k->...", n, rhat)
-        cos_graze = np.sqrt(np.clip(1.0 - ndotr * ndotr, 0.0, 1.0))
         c = 1.0 - 0.5 * cos_graze + rng.uniform(-conf_jitter, conf_jitter, size=z.shape)
         c = np.where(hit, np.clip(c, 0.0, 1.0), 0.0).astype(np.float32)
         if rig.depth_format == "u16":
@@ -354,7 +370,7 @@ def render_frame(rig: Rig, prims, seed: int, noise_k: float = 0.0015, zero_frac:
             raise ValueError(rig.depth_format)
         depth.append(np.ascontiguousarray(dep))
         conf.append(np.ascontiguousarray(c))
-        rgb.append(np.ascontiguousarray(np.where(hit[..., None], _colour_hash(pts), 0).astype(np.uint8)))
+        rgb.append(np.ascontiguousarray(col))
         if keep_truth:
             ztrue.append(z)
             sids.append(sid)
@@ -408,13 +424,15 @@ def config3_rig() -> Rig:
     return Rig(cams, "u16", 0.001)
 
 
-def config3(frame=0, keep_truth=False):
+def config3(frame=0, keep_truth=False, cache=None):
+    """8 x 1280x720 hemisphere rig; the scene is static, so ``cache`` may carry the
+    ray-cast between frames (only the sensor noise changes)."""
     rig = config3_rig()
     rng = np.random.default_rng(1000 * 3 + 999)
     objs = _ground_objects(rng, 20, 0.3, 3.2, 0.1, 0.6)
     prims = [Plane((0, 0, 1), 0.0)] + objs
     fr = render_frame(rig, prims, seed=1000 * 3 + frame, noise_k=0.0015, flying_frac=0.01,
-                      keep_truth=keep_truth)
+                      keep_truth=keep_truth, cache=cache)
     return rig, prims, fr
 
 
@@ -430,7 +448,7 @@ def fibonacci_rig(n, radius=5.0, f=512.0, size=1024) -> Rig:
     return Rig(cams, "u16", 0.001)
 
 
-def config4(n_cams=8, frame=0, keep_truth=False, size=1024):
+def config4(n_cams=8, frame=0, keep_truth=False, size=1024, cache=None):
     rig = fibonacci_rig(n_cams, 5.0, 512.0 * size / 1024, size)
     rng = np.random.default_rng(1000 * 4 + 999)
     prims = [Room((-8, -8, -8), (8, 8, 8)), Box((-0.6, -0.6, -0.6), (0.6, 0.6, 0.6))]
@@ -439,7 +457,7 @@ def config4(n_cams=8, frame=0, keep_truth=False, size=1024):
         v /= np.linalg.norm(v)
         prims.append(Sphere(tuple(4.0 * v), rng.uniform(0.2, 0.5)))
     fr = render_frame(rig, prims, seed=1000 * 4 + frame, noise_k=0.0015, flying_frac=0.01,
-                      keep_truth=keep_truth)
+                      keep_truth=keep_truth, cache=cache)
     return rig, prims, fr
 
 
