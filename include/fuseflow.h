@@ -174,6 +174,38 @@ int64_t fuseflow_capacity(const fuseflow_ctx *ctx);
 /* Device bytes held by the context (tables, scratch and outputs). */
 int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
 
+/* Allocation-free variant of fuseflow_fuse_frame (the paper has no counterpart; it is
+ * an engineering entry point).  Some callers cannot allocate device memory while they
+ * run: a host application that hands the whole GPU memory budget to its own pool up
+ * front, a real-time capture loop in which cudaMalloc's implicit device-wide
+ * synchronisation and unbounded latency are not acceptable, or a plug-in that must not
+ * change the process's memory footprint after start-up.  This call needs no context: it
+ * takes the rig and parameters directly, calls no cudaMalloc, cudaFree or other
+ * allocating routine (device or host), and keeps all of its scratch in one file-scope
+ * device array of about 15 MiB that every GPU loading this library holds until exit.
+ *
+ * Limits: at most 524,288 pixels per frame over all cameras, at most 65,536 ray-table
+ * entries (sum over cameras of width + height), and max_cells <= 32,768 (0 selects
+ * 32,768); larger requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.
+ * Inputs are device pointers as for fuseflow_fuse_frame; pos[3*max_cells],
+ * rgb_out[3*max_cells], weight, count, rep, key[max_cells] and *stats are caller-owned
+ * DEVICE outputs with the layout of fuseflow_cloud and fuseflow_stats.  Asynchronous on
+ * `stream`; errors found on the device appear in stats->error (bits as read by
+ * fuseflow_read_stats).
+ *
+ * The first call on each device looks the array's device address up with
+ * cudaGetSymbolAddress, empties its hash tables and synchronizes `stream`; make that
+ * first call before any stream capture.  Every later call reuses the array as the last
+ * call left it (each frame empties the tables it used again).  Calls whose GPU work
+ * overlaps, on several streams or from several host threads, race on the array: keep
+ * them ordered on one stream. */
+int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_extrinsics *extr,
+                               int32_t n_cams, const fuseflow_params *params,
+                               const void *const *depth, const float *const *conf,
+                               const uint8_t *const *rgb, float *pos, float *rgb_out,
+                               float *weight, uint32_t *count, uint32_t *rep, uint64_t *key,
+                               fuseflow_stats *stats, void *stream);
+
 /* Static description of a status code. */
 const char *fuseflow_status_string(int status);
 

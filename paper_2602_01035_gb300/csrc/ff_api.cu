@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -556,3 +557,262 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// Allocation-free variant of fuseflow_fuse_frame.
+//
+// All scratch (rig constants, ray tables, hash tables, per-pixel records, scan buffers)
+// lives in one file-scope device array of kStaticBytes (about 15 MiB), held by every GPU
+// that loads this library until the process exits.  Host code never dereferences the
+// array's name: the device address comes from cudaGetSymbolAddress, taken once per device
+// on that device's first call (which also clears the hash tables and synchronizes the
+// stream).  Later calls reuse the array; the frame's own clear and emit steps leave the
+// tables empty again, so calls in a row need no set-up.  Calls whose GPU work overlaps
+// (several streams, or several host threads) race on the array.
+namespace {
+
+constexpr long long kStaticMaxPixels = 1ll << 19;      // 524,288 pixels per frame
+constexpr long long kStaticMaxCells = 1ll << 15;       // 32,768 output cells
+constexpr unsigned kStaticSlots = 1u << 16;            // fine and coarse hash slots
+constexpr int kStaticMaxRays = 1 << 16;                // sum over cameras of W + H
+constexpr long long kStaticWords = kStaticMaxPixels / 32;
+constexpr int kStaticWBlocks = (int)((kStaticWords + 1023) / 1024);
+constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 1024 + 1);
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kSRig = 0;
+constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
+constexpr size_t kSMeta = al256(kSRays + sizeof(float2) * kStaticMaxRays);
+constexpr size_t kSAcc = al256(kSMeta + sizeof(SlotMeta) * kStaticSlots);
+constexpr size_t kSFused = al256(kSAcc + sizeof(SlotAcc) * kStaticSlots);
+constexpr size_t kSCKey = al256(kSFused + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSCCount = al256(kSCKey + sizeof(unsigned long long) * kStaticSlots);
+constexpr size_t kSCUsed = al256(kSCCount + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSBStats = al256(kSCnt + sizeof(FrameCounters) + sizeof(unsigned) * kStaticWords);
+constexpr size_t kSRec = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
+constexpr size_t kSWPre = al256(kSRec + sizeof(Rec) * kStaticMaxPixels);
+constexpr size_t kSBSum = al256(kSWPre + sizeof(unsigned) * kStaticWords);
+constexpr size_t kStaticBytes = al256(kSBSum + sizeof(unsigned) * kStaticWBlocks);
+static_assert(kStaticBytes <= (16u << 20), "static scratch must stay modest");
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mutex;                             // guards the host staging below
+unsigned char* g_static_dev[kStaticMaxDevices] = {};   // device address per device
+RigDev g_static_rig;                                   // host staging of the rig constants
+float2 g_static_rays[kStaticMaxRays];                  // host staging of the ray tables
+
+// The neighbour rule of neighbour_table() above (Sec. II.5(2)b: optical-axis angle, then
+// centre distance, then index, 1e-9 tolerance) on fixed-size arrays: no heap use.
+void neighbour_table_fixed(const fuseflow_extrinsics* ex, int n, int k1, int32_t* out) {
+  struct Cand { double angle, dist; int j; };
+  Cand cand[kMaxCams];
+  for (int i = 0; i < n; ++i) {
+    double ci[3], ai[3];
+    centre_axis(ex[i], ci, ai);
+    const double ni = std::sqrt(ai[0] * ai[0] + ai[1] * ai[1] + ai[2] * ai[2]);
+    int m = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double cj[3], aj[3];
+      centre_axis(ex[j], cj, aj);
+      const double nj = std::sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]);
+      double cs = (ai[0] * aj[0] + ai[1] * aj[1] + ai[2] * aj[2]) / (ni * nj);
+      cs = std::max(-1.0, std::min(1.0, cs));
+      const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+      cand[m++] = {std::acos(cs), std::sqrt(dx * dx + dy * dy + dz * dz), j};
+    }
+    for (int a = 1; a < m; ++a) {
+      const Cand v = cand[a];
+      int b = a;
+      auto before = [](const Cand& x, const Cand& y) {
+        if (std::fabs(x.angle - y.angle) > 1e-9) return x.angle < y.angle;
+        if (std::fabs(x.dist - y.dist) > 1e-9) return x.dist < y.dist;
+        return x.j < y.j;
+      };
+      while (b > 0 && before(v, cand[b - 1])) { cand[b] = cand[b - 1]; --b; }
+      cand[b] = v;
+    }
+    for (int q = 0; q < k1; ++q) out[i * k1 + q] = cand[q].j;
+  }
+}
+
+Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
+  Tables t{};
+  t.meta = reinterpret_cast<SlotMeta*>(base + kSMeta);
+  t.acc = reinterpret_cast<SlotAcc*>(base + kSAcc);
+  t.fused = reinterpret_cast<unsigned*>(base + kSFused);
+  t.fmask = kStaticSlots - 1;
+  t.ckey = reinterpret_cast<unsigned long long*>(base + kSCKey);
+  t.ccount = reinterpret_cast<unsigned*>(base + kSCCount);
+  t.cused = reinterpret_cast<unsigned*>(base + kSCUsed);
+  t.cmask = kStaticSlots - 1;
+  t.cnt = reinterpret_cast<FrameCounters*>(base + kSCnt);
+  t.bitmap = reinterpret_cast<unsigned*>(t.cnt + 1);
+  t.bstats = reinterpret_cast<BlockStats*>(base + kSBStats);
+  t.n_bstats = n_bstats;
+  t.rec = reinterpret_cast<Rec*>(base + kSRec);
+  t.wprefix = reinterpret_cast<unsigned*>(base + kSWPre);
+  t.bsum = reinterpret_cast<unsigned*>(base + kSBSum);
+  t.n_words = (n_px + 31) / 32;
+  t.n_wblocks = (int)((t.n_words + 1023) / 1024);
+  return t;
+}
+
+// Device address of the scratch array on the current device; the first call on a device
+// looks it up and empties its hash tables.
+int static_scratch(int dev, cudaStream_t s, unsigned char** out) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!g_static_dev[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return FUSEFLOW_ERR_CUDA;
+    unsigned char* base = static_cast<unsigned char*>(p);
+    const Tables t = static_tables(base, kStaticMaxPixels, kStaticBStats);
+    if (launch_init_tables(t, kStaticSlots, kStaticSlots, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+    g_static_dev[dev] = base;
+  }
+  *out = g_static_dev[dev];
+  return FUSEFLOW_OK;
+}
+
+}  // namespace
+
+extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
+                                          const fuseflow_extrinsics* extr, int32_t n_cams,
+                                          const fuseflow_params* params, const void* const* depth,
+                                          const float* const* conf, const uint8_t* const* rgb,
+                                          float* pos, float* rgb_out, float* weight,
+                                          uint32_t* count, uint32_t* rep, uint64_t* key,
+                                          fuseflow_stats* stats, void* stream) {
+  const int v = validate(intr, extr, n_cams, params);
+  if (v != FUSEFLOW_OK) return v;
+  if (!depth || !conf || !rgb || !pos || !rgb_out || !weight || !count || !rep || !key || !stats)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  long long n_px = 0, max_px = 0, n_rays = 0;
+  int tiles_max = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    const long long px = (long long)intr[i].width * intr[i].height;
+    n_px += px;
+    max_px = std::max(max_px, px);
+    n_rays += intr[i].width + intr[i].height;
+    tiles_max = std::max(tiles_max, ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16));
+    if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
+  }
+  const long long max_cells = params->max_cells > 0 ? params->max_cells : kStaticMaxCells;
+  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells)
+    return FUSEFLOW_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  unsigned char* base = nullptr;
+  int st = static_scratch(dev, s, &base);
+  if (st != FUSEFLOW_OK) return st;
+
+  // rig constants, the same quantities fuseflow_create derives (Eq. 4 relative poses,
+  // Sec. II.5(2)b neighbour table, ray tables), staged in host statics
+  const int K = std::min<int>(params->k_views, n_cams);
+  const int k1 = K - 1;
+  int32_t nbr[kMaxCams * kMaxK1];
+  neighbour_table_fixed(extr, n_cams, k1, nbr);
+  const double unit = params->depth_scale;
+  RigDev& rig = g_static_rig;
+  std::memset(&rig, 0, sizeof(rig));
+  rig.n_cams = n_cams;
+  rig.k1 = k1;
+  rig.tau = params->tau;
+  rig.use_conf = params->use_conf ? 1 : 0;
+  rig.use_cons = params->use_consistency ? 1 : 0;
+  rig.max_level = params->max_level;
+  rig.n_min = params->n_min;
+  rig.inv_s0u = (float)(unit / params->coarse_cell_m);
+  const double sig_u = params->sigma_m / unit;
+  if (k1 > 0) split(1.0 / (sig_u * sig_u * k1), rig.einv_h, rig.einv_l);
+  rig.depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
+  rig.n_px = n_px;
+  int nr = 0;
+  long long off = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    const fuseflow_intrinsics& k = intr[i];
+    const fuseflow_extrinsics& e = extr[i];
+    CamDev& c = rig.cam[i];
+    c.W = k.width;
+    c.H = k.height;
+    c.off = off;
+    off += (long long)k.width * k.height;
+    c.fx = (float)k.fx; c.fy = (float)k.fy; c.cx = (float)k.cx; c.cy = (float)k.cy;
+    split(k.fx, c.fxh, c.fxl);
+    split(k.fy, c.fyh, c.fyl);
+    split(k.cx, c.cxh, c.cxl);
+    split(k.cy, c.cyh, c.cyl);
+    double cen[3], ax[3];
+    centre_axis(e, cen, ax);
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) c.Rwc[3 * r + q] = (float)e.R[3 * q + r];
+      c.cwc[r] = (float)(cen[r] / unit);
+    }
+    c.ray_x = nr;
+    for (int x = 0; x < k.width; ++x, ++nr) split(((double)x - k.cx) / k.fx, g_static_rays[nr].x, g_static_rays[nr].y);
+    c.ray_y = nr;
+    for (int y = 0; y < k.height; ++y, ++nr) split(((double)y - k.cy) / k.fy, g_static_rays[nr].x, g_static_rays[nr].y);
+    c.pair0 = i * k1;
+    for (int q = 0; q < k1; ++q) {
+      const int j = nbr[i * k1 + q];
+      const fuseflow_extrinsics& ej = extr[j];
+      PairDev& P = rig.pair[c.pair0 + q];
+      P.j = j;
+      double Rji[9], tji[3];
+      for (int r = 0; r < 3; ++r)
+        for (int s2 = 0; s2 < 3; ++s2) {
+          double acc = 0;
+          for (int m = 0; m < 3; ++m) acc += ej.R[3 * r + m] * e.R[3 * s2 + m];
+          Rji[3 * r + s2] = acc;
+        }
+      for (int r = 0; r < 3; ++r)
+        tji[r] = ej.t[r] - (Rji[3 * r] * e.t[0] + Rji[3 * r + 1] * e.t[1] + Rji[3 * r + 2] * e.t[2]);
+      for (int a = 0; a < 9; ++a) split(Rji[a], P.Rh[a], P.Rl[a]);
+      for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
+    }
+  }
+  // pageable host -> device copies return once the host buffers have been read
+  if (cudaMemcpyAsync(base + kSRig, &rig, sizeof(RigDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + kSRays, g_static_rays, sizeof(float2) * (size_t)nr, cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+
+  Geometry geo{};
+  geo.n_cams = n_cams;
+  geo.depth_f32 = rig.depth_f32;
+  geo.count_blocks_x = (int)((max_px + 1023) / 1024);
+  geo.tiles_max = tiles_max;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  geo.emit_blocks = std::max(1, sms * 4);
+  const Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
+  OutDev od{};
+  od.stats = stats;
+  od.pos = pos;
+  od.rgb = rgb_out;
+  od.weight = weight;
+  od.count = count;
+  od.rep = rep;
+  od.key = reinterpret_cast<unsigned long long*>(key);
+  od.max_cells = max_cells;
+  od.s0_m = params->coarse_cell_m;
+  od.unit_m = unit;
+  FramePtrs fp{};
+  for (int i = 0; i < n_cams; ++i) {
+    fp.depth[i] = depth[i];
+    fp.conf[i] = conf[i];
+    fp.rgb[i] = rgb[i];
+  }
+  const cudaError_t e = launch_frame(reinterpret_cast<const RigDev*>(base + kSRig),
+                                     reinterpret_cast<const float2*>(base + kSRays), fp, t,
+                                     TraceDev{}, od, geo, s, nullptr);
+  return e == cudaSuccess ? FUSEFLOW_OK : FUSEFLOW_ERR_CUDA;
+}

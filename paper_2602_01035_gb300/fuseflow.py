@@ -87,6 +87,12 @@ EXPORTS = {
     "fuseflow_enable_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "fuseflow_read_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "fuseflow_stage_name": (C.c_char_p, [C.c_int]),
+    "fuseflow_fuse_frame_static": (C.c_int, [C.POINTER(fuseflow_intrinsics),
+                                             C.POINTER(fuseflow_extrinsics), C.c_int32,
+                                             C.POINTER(fuseflow_params), C.POINTER(C.c_void_p),
+                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 FUSEFLOW_N_STAGES = 6
 
@@ -218,6 +224,17 @@ def fuseflow_capacity(ctx) -> int:
 
 def fuseflow_device_bytes(ctx) -> int:
     return int(load().fuseflow_device_bytes(ctx))
+
+
+def fuseflow_fuse_frame_static(intr, extr, n_cams: int, params: fuseflow_params, depth_ptrs,
+                               conf_ptrs, rgb_ptrs, pos, rgb_out, weight, count, rep, key, stats,
+                               stream: int = 0) -> int:
+    """Allocation-free fusion of one frame (device inputs and outputs); returns the status."""
+    return load().fuseflow_fuse_frame_static(
+        intr, extr, n_cams, C.byref(params), _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+        _ptr_array(rgb_ptrs), C.c_void_p(pos), C.c_void_p(rgb_out), C.c_void_p(weight),
+        C.c_void_p(count), C.c_void_p(rep), C.c_void_p(key), C.c_void_p(stats),
+        C.c_void_p(stream))
 
 
 def fuseflow_enable_stage_timing(ctx, enable: bool) -> None:
