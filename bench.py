@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "depth px/s and frames/s at 8x1280x720 views; p50/p99 latency, served vs plain"
-KERNELS_PER_FRAME = 6      # count, assign, accumulate, scan words, scan blocks, emit
+KERNELS_PER_FRAME = 6      # count, assign, reduce, scan words, scan blocks, emit
 CELL_OUT_BYTES = 44        # pos 12 + rgb 12 + weight 4 + count 4 + rep 4 + key 8
 
 
@@ -129,9 +129,7 @@ def roofline_model(stage: str, px: int, cells: float, depth_bytes: int):
     if stage == "count":
         return depth_bytes * px + 4 * px            # depth + confidence
     if stage == "assign":
-        return depth_bytes * px + 4 * px            # depth + confidence (gathers hit L2)
-    if stage == "accumulate":
-        return depth_bytes * px + 3 * px            # depth + colour
+        return depth_bytes * px + 4 * px + 3 * px   # depth + confidence + colour (gathers hit L2)
     if stage == "emit":
         return CELL_OUT_BYTES * cells
     return None

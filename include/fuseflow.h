@@ -160,8 +160,8 @@ int fuseflow_get_neighbours(const fuseflow_ctx *ctx, int32_t *out, int32_t *k_mi
  * events between its stages on its own stream (a ring of the last 1024 frames).
  * fuseflow_read_stage_times waits for the last recorded event, writes the summed
  * milliseconds of each of the FUSEFLOW_N_STAGES stages to ms[] and the number of frames
- * to *n_frames, then resets the ring.  Stages: 0 clear, 1 count (a), 2 assign (b, c),
- * 3 accumulate (d), 4 scan, 5 emit. */
+ * to *n_frames, then resets the ring.  Stages: 0 clear, 1 count (a, c2), 2 assign
+ * (b, c, d per tile), 3 reduce (d per cell), 4 scan, 5 emit. */
 #define FUSEFLOW_N_STAGES 6
 int fuseflow_enable_stage_timing(fuseflow_ctx *ctx, int enable);
 int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
@@ -182,11 +182,13 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
  * change the process's memory footprint after start-up.  This call needs no context: it
  * takes the rig and parameters directly, calls no cudaMalloc, cudaFree or other
  * allocating routine (device or host), and keeps all of its scratch in one file-scope
- * device array of about 15 MiB that every GPU loading this library holds until exit.
+ * device array of about 17 MiB that every GPU loading this library holds until exit.
  *
  * Limits: at most 524,288 pixels per frame over all cameras, at most 65,536 ray-table
  * entries (sum over cameras of width + height), and max_cells <= 32,768 (0 selects
- * 32,768); larger requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.
+ * 32,768); larger requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.  A
+ * frame that produces more than 131,072 (tile, cell) partial records reports a capacity
+ * error in stats->error.
  * Inputs are device pointers as for fuseflow_fuse_frame; pos[3*max_cells],
  * rgb_out[3*max_cells], weight, count, rep, key[max_cells] and *stats are caller-owned
  * DEVICE outputs with the layout of fuseflow_cloud and fuseflow_stats.  Asynchronous on

@@ -304,15 +304,18 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const int n_bstats = ctx->geo.count_blocks_x * n_cams;
   size_t o = 0;
   auto take = [&](size_t bytes, size_t align) { o = align_up(o, align); size_t at = o; o += bytes; return at; };
-  const size_t o_meta = take(sizeof(SlotMeta) * ctx->fcap, 256);
-  const size_t o_acc = take(sizeof(SlotAcc) * ctx->fcap, 256);
+  // (tile, cell) partials: at most one per gated pixel
+  const unsigned max_partials = (unsigned)std::min<long long>(off, 0xfffffffell);
+  const size_t o_fkey = take(sizeof(unsigned long long) * ctx->fcap, 256);
+  const size_t o_fhead = take(sizeof(unsigned) * ctx->fcap, 256);
   const size_t o_fused = take(sizeof(unsigned) * ctx->fcap, 256);
   const size_t o_ckey = take(sizeof(unsigned long long) * ctx->ccap, 256);
   const size_t o_ccnt = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
-  const size_t o_rec = take(sizeof(Rec) * (size_t)off, 256);
+  const size_t o_part = take(sizeof(Partial) * (size_t)max_partials, 256);
+  const size_t o_staged = take(sizeof(CellOut) * ctx->fcap, 256);
   const size_t o_wpre = take(sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bsum = take(sizeof(unsigned) * (size_t)n_wblocks, 256);
   ctx->table_bytes = o;
@@ -336,8 +339,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   if (status == FUSEFLOW_OK) {
     char* b = static_cast<char*>(ctx->d_tables);
     Tables& t = ctx->tab;
-    t.meta = reinterpret_cast<SlotMeta*>(b + o_meta);
-    t.acc = reinterpret_cast<SlotAcc*>(b + o_acc);
+    t.fkey = reinterpret_cast<unsigned long long*>(b + o_fkey);
+    t.fhead = reinterpret_cast<unsigned*>(b + o_fhead);
     t.fused = reinterpret_cast<unsigned*>(b + o_fused);
     t.fmask = ctx->fcap - 1;
     t.ckey = reinterpret_cast<unsigned long long*>(b + o_ckey);
@@ -348,7 +351,9 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     t.bitmap = reinterpret_cast<unsigned*>(t.cnt + 1);
     t.bstats = reinterpret_cast<BlockStats*>(b + o_bst);
     t.n_bstats = n_bstats;
-    t.rec = reinterpret_cast<Rec*>(b + o_rec);
+    t.part = reinterpret_cast<Partial*>(b + o_part);
+    t.max_partials = max_partials;
+    t.staged = reinterpret_cast<CellOut*>(b + o_staged);
     t.wprefix = reinterpret_cast<unsigned*>(b + o_wpre);
     t.bsum = reinterpret_cast<unsigned*>(b + o_bsum);
     t.n_words = n_words;
@@ -433,7 +438,8 @@ int fuseflow_read_stats(fuseflow_ctx* ctx, fuseflow_stats* host_stats, void* str
     return FUSEFLOW_ERR_CUDA;
   const unsigned err = (unsigned)host_stats->error;
   if (err & (kErrFineFull | kErrCoarseFull | kErrCells)) return FUSEFLOW_ERR_CAPACITY;
-  if (err & kErrCoarseMiss) return FUSEFLOW_ERR_INTERNAL;
+  if (err & kErrPartials) return FUSEFLOW_ERR_CAPACITY;
+  if (err & (kErrCoarseMiss | kErrList)) return FUSEFLOW_ERR_INTERNAL;
   return FUSEFLOW_OK;
 }
 
@@ -545,7 +551,7 @@ int fuseflow_read_stage_times(fuseflow_ctx* ctx, double* ms, int64_t* n_frames) 
 }
 
 const char* fuseflow_stage_name(int stage) {
-  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "accumulate", "scan",
+  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "reduce", "scan",
                                                  "emit"};
   return (stage >= 0 && stage < FUSEFLOW_N_STAGES) ? names[stage] : "unknown";
 }
@@ -562,7 +568,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
 // Allocation-free variant of fuseflow_fuse_frame.
 //
 // All scratch (rig constants, ray tables, hash tables, per-pixel records, scan buffers)
-// lives in one file-scope device array of kStaticBytes (about 15 MiB), held by every GPU
+// lives in one file-scope device array of kStaticBytes (about 17 MiB), held by every GPU
 // that loads this library until the process exits.  Host code never dereferences the
 // array's name: the device address comes from cudaGetSymbolAddress, taken once per device
 // on that device's first call (which also clears the hash tables and synchronizes the
@@ -572,6 +578,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
 namespace {
 
 constexpr long long kStaticMaxPixels = 1ll << 19;      // 524,288 pixels per frame
+constexpr unsigned kStaticMaxPartials = 1u << 17;      // (tile, cell) partial records
 constexpr long long kStaticMaxCells = 1ll << 15;       // 32,768 output cells
 constexpr unsigned kStaticSlots = 1u << 16;            // fine and coarse hash slots
 constexpr int kStaticMaxRays = 1 << 16;                // sum over cameras of W + H
@@ -583,19 +590,20 @@ constexpr int kStaticMaxDevices = 64;
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kSRig = 0;
 constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
-constexpr size_t kSMeta = al256(kSRays + sizeof(float2) * kStaticMaxRays);
-constexpr size_t kSAcc = al256(kSMeta + sizeof(SlotMeta) * kStaticSlots);
-constexpr size_t kSFused = al256(kSAcc + sizeof(SlotAcc) * kStaticSlots);
+constexpr size_t kSFKey = al256(kSRays + sizeof(float2) * kStaticMaxRays);
+constexpr size_t kSFHead = al256(kSFKey + sizeof(unsigned long long) * kStaticSlots);
+constexpr size_t kSFused = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSCKey = al256(kSFused + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSCCount = al256(kSCKey + sizeof(unsigned long long) * kStaticSlots);
 constexpr size_t kSCUsed = al256(kSCCount + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSBStats = al256(kSCnt + sizeof(FrameCounters) + sizeof(unsigned) * kStaticWords);
-constexpr size_t kSRec = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
-constexpr size_t kSWPre = al256(kSRec + sizeof(Rec) * kStaticMaxPixels);
+constexpr size_t kSPart = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
+constexpr size_t kSStaged = al256(kSPart + sizeof(Partial) * kStaticMaxPartials);
+constexpr size_t kSWPre = al256(kSStaged + sizeof(CellOut) * kStaticSlots);
 constexpr size_t kSBSum = al256(kSWPre + sizeof(unsigned) * kStaticWords);
 constexpr size_t kStaticBytes = al256(kSBSum + sizeof(unsigned) * kStaticWBlocks);
-static_assert(kStaticBytes <= (16u << 20), "static scratch must stay modest");
+static_assert(kStaticBytes <= (18u << 20), "static scratch must stay modest");
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -641,8 +649,8 @@ void neighbour_table_fixed(const fuseflow_extrinsics* ex, int n, int k1, int32_t
 
 Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   Tables t{};
-  t.meta = reinterpret_cast<SlotMeta*>(base + kSMeta);
-  t.acc = reinterpret_cast<SlotAcc*>(base + kSAcc);
+  t.fkey = reinterpret_cast<unsigned long long*>(base + kSFKey);
+  t.fhead = reinterpret_cast<unsigned*>(base + kSFHead);
   t.fused = reinterpret_cast<unsigned*>(base + kSFused);
   t.fmask = kStaticSlots - 1;
   t.ckey = reinterpret_cast<unsigned long long*>(base + kSCKey);
@@ -653,7 +661,9 @@ Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   t.bitmap = reinterpret_cast<unsigned*>(t.cnt + 1);
   t.bstats = reinterpret_cast<BlockStats*>(base + kSBStats);
   t.n_bstats = n_bstats;
-  t.rec = reinterpret_cast<Rec*>(base + kSRec);
+  t.part = reinterpret_cast<Partial*>(base + kSPart);
+  t.max_partials = kStaticMaxPartials;
+  t.staged = reinterpret_cast<CellOut*>(base + kSStaged);
   t.wprefix = reinterpret_cast<unsigned*>(base + kSWPre);
   t.bsum = reinterpret_cast<unsigned*>(base + kSBSum);
   t.n_words = (n_px + 31) / 32;

@@ -30,6 +30,8 @@ constexpr unsigned kErrFineFull = 1u;    // fine hash table could not take a key
 constexpr unsigned kErrCoarseFull = 2u;  // coarse hash table could not take a key
 constexpr unsigned kErrCells = 4u;       // more cells than the output capacity
 constexpr unsigned kErrCoarseMiss = 8u;  // a point's coarse cell was not found (internal)
+constexpr unsigned kErrPartials = 16u;   // more (tile, cell) partials than the buffer holds
+constexpr unsigned kErrList = 32u;       // a cell list was longer than the partials written
 
 struct CamDev {
   int W, H;
@@ -65,29 +67,35 @@ struct RigDev {
   PairDev pair[kMaxCams * kMaxK1];
 };
 
-// One entry per fine cell (hash slot); cleared by the emit step after use.
-struct __align__(32) SlotMeta {
-  unsigned long long key;        // cell key or kKeyEmpty
-  unsigned long long rep;        // max of (float bits of C) << 32 | ~g
-  int mmin;                      // smallest binary exponent m of a member weight
-  unsigned count;                // members
-  unsigned long long pad;
+// Per (tile, cell) partial result of the assign step, linked into its cell's list.
+// Sums are exact integers in units of 2^-(kFixShift + mmin) of the tile's own smallest
+// weight exponent mmin; the reduce step shifts them to the cell's smallest exponent.
+struct __align__(16) Partial {
+  unsigned next;                 // next partial of the same cell, or kSlotNone
+  unsigned count;                // members in the tile
+  int mmin;                      // smallest weight exponent m in the tile
+  unsigned pad;
+  unsigned long long rep;        // max of ordered(C) << 32 | ~g
+  unsigned long long s[7];       // sums of w, w frac_x, w frac_y, w frac_z, w r, w g, w b
 };
+static_assert(sizeof(Partial) == 80, "partial record layout");
 
-struct __align__(64) SlotAcc {   // exact integer sums in units of 2^-(kFixShift + mmin)
-  unsigned long long w, x, y, z, r, g, b, pad;
+// Fused cell staged by the reduce step (indexed by insertion order) for the emit step.
+struct __align__(16) CellOut {
+  float pos[3];
+  float rgb[3];
+  float weight;
+  unsigned count;
+  unsigned rep;
+  unsigned pad;
+  unsigned long long key;
 };
-
-struct Rec {                     // per pixel, written by the assign step
-  uint32_t slot;                 // fine slot or kSlotNone
-  float mu;                      // weight mantissa: omega = mu * 2^-m
-  int m;
-};
+static_assert(sizeof(CellOut) == 48, "staged cell layout");
 
 struct FrameCounters {
   unsigned n_cells, n_coarse;
   unsigned error;
-  unsigned pad;
+  unsigned n_partials;
 };
 
 struct BlockStats {              // per block of the coarse-count step

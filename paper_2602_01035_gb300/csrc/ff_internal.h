@@ -16,8 +16,8 @@ struct FramePtrs {               // one frame's caller-owned device images, per 
 };
 
 struct Tables {                  // context-owned device scratch
-  SlotMeta* meta;                // fine hash table, fcap entries
-  SlotAcc* acc;
+  unsigned long long* fkey;      // fine hash table keys, fcap entries
+  unsigned* fhead;               // first partial of each fine cell, kSlotNone if none
   unsigned* fused;               // used fine slots, in insertion order
   unsigned fmask;                // fcap - 1
   unsigned long long* ckey;      // coarse hash table, ccap entries
@@ -27,7 +27,9 @@ struct Tables {                  // context-owned device scratch
   FrameCounters* cnt;
   BlockStats* bstats;            // one per block of the coarse-count step
   int n_bstats;
-  Rec* rec;                      // one per pixel
+  Partial* part;                 // (tile, cell) partials, max_partials entries
+  unsigned max_partials;
+  CellOut* staged;               // fused cells by insertion order, fcap entries
   unsigned* bitmap;              // representative bitmap, one bit per pixel
   unsigned* wprefix;             // per-word exclusive prefix within its 1024-word block
   unsigned* bsum;                // per 1024-word block: exclusive prefix after the scan

@@ -6,14 +6,18 @@
 //            per-block pixel counts and extent (Sec. II.5(1)b)
 //   assign   (b) consistency V (Eq. 4-7), omega = C V (Eq. 10) as mantissa/exponent;
 //            (c) level per coarse cell (Sec. II.5(1)d), cell key (Sec. II.5(1)e), fine
-//            hash insertion; per-cell member count, representative (Sec. II.5(2)a) and
-//            smallest weight exponent
-//   accum    (d) exact fixed-point sums of omega, omega P, omega RGB per cell (Eq. 11)
+//            hash insertion; (d) per (tile, cell): member count, representative
+//            (Sec. II.5(2)a), smallest weight exponent and exact fixed-point sums of
+//            omega, omega P, omega RGB (Eq. 11), written as one partial record linked
+//            into the cell's list
+//   reduce   per cell: walk its partials, combine them, stage the fused cell, mark its
+//            representative; the used hash slots are cleared for the next frame
 //   scan     ranks of the representatives (output order), frame statistics
-//   emit     fused cells, then the used hash slots are cleared for the next frame
+//   emit     fused cells in representative order
 //
-// Reductions are order-independent: integer atomics only (counts, max, min and
-// fixed-point sums), so the output is bitwise reproducible.
+// Every reduction is order-independent (integer counts, max, min and fixed-point sums,
+// warp-level first, then shared memory, then one record per tile and cell), so the output
+// is bitwise reproducible.
 #include <climits>
 #include <cstdint>
 
@@ -37,10 +41,10 @@ constexpr float kInvLn2 = 1.44269504088896340736f;
 __device__ __forceinline__ unsigned fine_insert(const Tables& t, unsigned long long key) {
   unsigned h = (unsigned)mix64(key) & t.fmask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    unsigned long long cur = __ldcg(&t.meta[h].key);
+    unsigned long long cur = __ldcg(&t.fkey[h]);
     if (cur == key) return h;
     if (cur == kKeyEmpty) {
-      cur = atomicCAS(&t.meta[h].key, kKeyEmpty, key);
+      cur = atomicCAS(&t.fkey[h], kKeyEmpty, key);
       if (cur == kKeyEmpty) {
         const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
         if (n <= t.fmask) t.fused[n] = h;
@@ -91,11 +95,30 @@ template <int TS, typename K>
 __device__ __forceinline__ int local_pos(K* tab, K empty, K key) {
   unsigned h = (unsigned)mix64((unsigned long long)key) & (TS - 1);
   for (int probe = 0; probe < TS; ++probe) {
-    const K prev = atomicCAS(&tab[h], empty, key);
-    if (prev == empty || prev == key) return (int)h;
+    const K cur = *static_cast<volatile K*>(&tab[h]);
+    if (cur == key) return (int)h;
+    if (cur == empty) {
+      const K prev = atomicCAS(&tab[h], empty, key);
+      if (prev == empty || prev == key) return (int)h;
+    }
     h = (h + 1) & (TS - 1);
   }
   return -1;
+}
+
+// ------------------------------------------------------------------ block constants
+// The tile's camera, its K-1 neighbour pairs and the neighbour cameras, staged in shared
+// memory once per block (every pixel of a tile belongs to the same camera).
+struct BlockConst {
+  CamDev cam;
+  PairDev pair[kMaxK1];
+  CamDev nb[kMaxK1];
+};
+
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes) {
+  int* d = static_cast<int*>(dst);
+  const int* s = static_cast<const int*>(src);
+  for (int i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
 }
 
 // ------------------------------------------------------------------ Eq. 4-7 per point
@@ -117,7 +140,7 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 
 // Sum over the K-1 neighbour views of d_ij^2 (Eq. 6) in depth units^2, as ff (sh, sl).
 template <typename DT>
-__device__ __forceinline__ void residual_sum(const RigDev& rig, const CamDev& C,
+__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1,
                                              const float2* __restrict__ rays,
                                              const FramePtrs& fp, float z, float2 rx, float2 ry,
                                              float& sh, float& sl, int& nview) {
@@ -129,9 +152,9 @@ __device__ __forceinline__ void residual_sum(const RigDev& rig, const CamDev& C,
   sh = 0.0f;
   sl = 0.0f;
   nview = 0;
-  for (int q = 0; q < rig.k1; ++q) {
-    const PairDev& P = rig.pair[C.pair0 + q];
-    const CamDev& J = rig.cam[P.j];
+  for (int q = 0; q < k1; ++q) {
+    const PairDev& P = bc.pair[q];
+    const CamDev& J = bc.nb[q];
     float a[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -169,7 +192,7 @@ __device__ __forceinline__ void residual_sum(const RigDev& rig, const CamDev& C,
     const int py = tie_v ? exact_round(J.fyh, J.fyl, J.cyh, J.cyl, ah[1], al[1], ah[2], al[2], rv)
                          : (int)floorf(fv);
     if (px < 0 || px >= J.W || py < 0 || py >= J.H) continue;   // field-of-view check
-    const DT Dj = static_cast<const DT*>(fp.depth[P.j])[(long long)py * J.W + px];
+    const DT Dj = __ldg(static_cast<const DT*>(fp.depth[P.j]) + (long long)py * J.W + px);
     if (!Depth<DT>::valid(Dj)) continue;
     if (!have) {
 #pragma unroll
@@ -179,7 +202,7 @@ __device__ __forceinline__ void residual_sum(const RigDev& rig, const CamDev& C,
     }
     // Eq. 5: Q = D_j(u_j) (rx_j, ry_j, 1) in camera-j coordinates (rigid motion keeps d).
     const float zj = Depth<DT>::z(Dj);
-    const float2 qx = rays[J.ray_x + px], qy = rays[J.ray_y + py];
+    const float2 qx = __ldg(rays + J.ray_x + px), qy = __ldg(rays + J.ray_y + py);
     float qh[3], ql[3];
     two_prod(zj, qx.x, qh[0], ql[0]);
     ql[0] = __fmaf_rn(zj, qx.y, ql[0]);
@@ -235,7 +258,7 @@ __device__ __forceinline__ void load4(const DT* __restrict__ d, const float* __r
 }
 
 template <typename DT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
         int blocks_x) {
   constexpr int TS = 2 * kCountBlockPx;
@@ -261,10 +284,13 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
   const long long p0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * kCountPx;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   DT dv[4];
   float cv[4];
   unsigned nv = 0, ng = 0, noor = 0;
   unsigned bmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, bmax[3] = {0u, 0u, 0u};
+  unsigned long long rk[kCountPx] = {kKeyEmpty, kKeyEmpty, kKeyEmpty, kKeyEmpty};
+  unsigned rn[kCountPx] = {1u, 1u, 1u, 1u};
   if (p0 < npx) {
     load4<DT>(dep, cf, p0, npx, dv, cv);
     int y = (int)(p0 / C.W);
@@ -276,27 +302,36 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
         if (!rig.use_conf || cv[k] > rig.tau) {       // Eq. 9
           ++ng;
           float P[3], r[3];
-          world_point(C, Depth<DT>::z(dv[k]), rays[C.ray_x + x].x, rays[C.ray_y + y].x, P);
+          world_point(C, Depth<DT>::z(dv[k]), __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const unsigned o = ordered(P[a]);
             bmin[a] = min(bmin[a], o);
             bmax[a] = max(bmax[a], o);
           }
-          if (grid_coords(rig, P, r)) {
-            const int h = local_pos<TS>(s_key, kKeyEmpty, coarse_key(r));
-            if (h >= 0) atomicAdd(&s_cnt[h], 1u);
-            else atomicOr(&t.cnt->error, kErrCoarseFull);
-          } else {
-            ++noor;
-          }
+          if (grid_coords(rig, P, r)) rk[k] = coarse_key(r);
+          else ++noor;
         }
       }
       if (++x == C.W) { x = 0; ++y; }
     }
   }
+  // Sec. II.5(1)c density estimate: merge the thread's equal neighbours, then one
+  // shared-memory update per distinct key and thread
+#pragma unroll
+  for (int k = 1; k < kCountPx; ++k)
+    if (rk[k] != kKeyEmpty && rk[k] == rk[k - 1]) {
+      rn[k] += rn[k - 1];
+      rk[k - 1] = kKeyEmpty;
+    }
+#pragma unroll
+  for (int j = 0; j < kCountPx; ++j) {
+    if (rk[j] == kKeyEmpty) continue;
+    const int h = local_pos<TS>(s_key, kKeyEmpty, rk[j]);
+    if (h >= 0) atomicAdd(&s_cnt[h], rn[j]);
+    else atomicOr(&t.cnt->error, kErrCoarseFull);
+  }
   // per-block pixel counts and extent
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned vals[9] = {nv, ng, noor, bmin[0], bmin[1], bmin[2], bmax[0], bmax[1], bmax[2]};
   vals[0] = __reduce_add_sync(0xffffffffu, vals[0]);
   vals[1] = __reduce_add_sync(0xffffffffu, vals[1]);
@@ -322,7 +357,6 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     }
     t.bstats[bid] = b;
   }
-  // flush the block's coarse counts (Sec. II.5(1)c density estimate)
   for (int i = threadIdx.x; i < TS; i += kThreads) {
     const unsigned long long key = s_key[i];
     if (key == kKeyEmpty) continue;
@@ -332,250 +366,335 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
 }
 
 // ------------------------------------------------------------------ assign step
+constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
+constexpr int kAssignNL = kTilePx;         // distinct fine cells of a tile, at most
+constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+constexpr size_t kSmBC = 0;
+constexpr size_t kSmCK = align16(kSmBC + sizeof(BlockConst));      // u64[TS] coarse keys
+constexpr size_t kSmCL = align16(kSmCK + 8 * kAssignTS);           // u8[TS] coarse levels
+constexpr size_t kSmFK = align16(kSmCL + kAssignTS);               // u64[TS] fine keys
+constexpr size_t kSmFI = align16(kSmFK + 8 * kAssignTS);           // int[TS] entry of a position
+constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64[NL] key of an entry
+constexpr size_t kSmAcc = align16(kSmEK + 8 * kAssignNL);          // u32[14][NL] split sums
+constexpr size_t kSmCnt = align16(kSmAcc + 14 * 4 * kAssignNL);    // u32[NL] members
+constexpr size_t kSmCmax = align16(kSmCnt + 4 * kAssignNL);        // u32[NL] largest ordered C
+constexpr size_t kSmGmin = align16(kSmCmax + 4 * kAssignNL);       // u32[NL] lowest index at it
+constexpr size_t kSmMin = align16(kSmGmin + 4 * kAssignNL);        // int[NL] smallest exponent
+constexpr size_t kSmPid = align16(kSmMin + 4 * kAssignNL);         // u16[tile] gated pixels
+constexpr size_t kAssignSmem = align16(kSmPid + 2 * kTilePx);
+constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
+
 template <typename DT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m) {
-  constexpr int TS = 2 * kTilePx;
-  __shared__ unsigned long long s_ck[TS];
-  __shared__ unsigned char s_cl[TS];
-  __shared__ unsigned long long s_fk[TS];
-  __shared__ unsigned s_fcnt[TS];
-  __shared__ unsigned long long s_frep[TS];
-  __shared__ int s_fmin[TS];
-  __shared__ unsigned s_fslot[TS];
+  extern __shared__ __align__(16) unsigned char smem[];
+  BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
+  unsigned long long* s_ck = reinterpret_cast<unsigned long long*>(smem + kSmCK);
+  unsigned char* s_cl = smem + kSmCL;
+  unsigned long long* s_fk = reinterpret_cast<unsigned long long*>(smem + kSmFK);
+  int* s_fi = reinterpret_cast<int*>(smem + kSmFI);
+  unsigned long long* s_ek = reinterpret_cast<unsigned long long*>(smem + kSmEK);
+  unsigned* s_acc = reinterpret_cast<unsigned*>(smem + kSmAcc);
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(smem + kSmCnt);
+  unsigned* s_cmax = reinterpret_cast<unsigned*>(smem + kSmCmax);
+  unsigned* s_gmin = reinterpret_cast<unsigned*>(smem + kSmGmin);
+  int* s_min = reinterpret_cast<int*>(smem + kSmMin);
+  unsigned short* s_pid = reinterpret_cast<unsigned short*>(smem + kSmPid);
+  __shared__ unsigned s_n, s_base, s_ng;
+  __shared__ unsigned s_wc[2 * (kThreads / 32)];
+
   const RigDev& rig = *rigp;
   const int cam = blockIdx.y;
-  const CamDev& C = rig.cam[cam];
-  const int tiles_x = (C.W + kTileW - 1) / kTileW;
-  const int tiles_y = (C.H + kTileH - 1) / kTileH;
+  const int W = rig.cam[cam].W, H = rig.cam[cam].H;
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  const int tiles_y = (H + kTileH - 1) / kTileH;
   if ((int)blockIdx.x >= tiles_x * tiles_y) return;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < TS; i += kThreads) {
+  const int k1 = rig.k1;
+  copy_words(&bc.cam, &rig.cam[cam], sizeof(CamDev));
+  for (int q = 0; q < k1; ++q) {
+    const PairDev& src = rig.pair[rig.cam[cam].pair0 + q];
+    copy_words(&bc.pair[q], &src, sizeof(PairDev));
+    copy_words(&bc.nb[q], &rig.cam[src.j], sizeof(CamDev));
+  }
+  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
     s_ck[i] = kKeyEmpty;
     s_fk[i] = kKeyEmpty;
-    s_fcnt[i] = 0;
-    s_frep[i] = 0ull;
-    s_fmin[i] = INT_MAX;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) s_n = 0;
 
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
+  const uint8_t* __restrict__ col = fp.rgb[cam];
   const bool trace = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
+  const float qnan = __int_as_float(0x7fc00000);
+
+  // (a) Eq. 9 gate, then compaction of the tile's gated pixels so that the per-point work
+  // below runs on full warps
+  unsigned gmask[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int row = warp + 8 * k;
+    const int x = tx * kTileW + lane, y = ty * kTileH + row;
+    bool gated = false;
+    if (x < W && y < H) {
+      const long long li = (long long)y * W + x;
+      const DT D = dep[li];
+      gated = Depth<DT>::valid(D) && (!rig.use_conf || cf[li] > rig.tau);
+      if (!gated && trace) {
+        const long long g = rig.cam[cam].off + li;
+        if (tr.pw) { tr.pw[3 * g] = qnan; tr.pw[3 * g + 1] = qnan; tr.pw[3 * g + 2] = qnan; }
+        if (tr.e) tr.e[g] = qnan;
+        if (tr.omega) tr.omega[g] = qnan;
+        if (tr.nview) tr.nview[g] = -1;
+        if (tr.key) tr.key[g] = kKeyEmpty;
+      }
+    }
+    gmask[k] = __ballot_sync(0xffffffffu, gated);
+    if (lane == 0) s_wc[row] = __popc(gmask[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {            // exclusive scan of the 16 row counts
+    const unsigned v = threadIdx.x < 16 ? s_wc[threadIdx.x] : 0u;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (threadIdx.x < 16) s_wc[threadIdx.x] = x - v;
+    if (threadIdx.x == 15) s_ng = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int row = warp + 8 * k;
+    if ((gmask[k] >> lane) & 1u)
+      s_pid[s_wc[row] + __popc(gmask[k] & ((1u << lane) - 1u))] = (unsigned short)(row * kTileW + lane);
+  }
+  __syncthreads();
+  const int n_g = (int)s_ng;
+  const CamDev& C = bc.cam;
+
+  // (a) + (b): back-project, consistency, weight; coarse cell of each gated point
   float r[2][3];
   bool has[2] = {false, false};
-  bool inb[2] = {false, false};
   float mu[2] = {0.0f, 0.0f};
   int mexp[2] = {0, 0};
-  unsigned long long rank[2] = {0ull, 0ull};
-  int hc[2] = {-1, -1}, hf[2] = {-1, -1};
-  long long gi[2] = {0, 0};
+  unsigned cord[2] = {0u, 0u};
+  int hpos[2] = {0, 0};
+  long long gi[2] = {0, 0}, li[2] = {0, 0};
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int x = tx * kTileW + lane, y = ty * kTileH + warp + 8 * k;
-    if (x >= C.W || y >= C.H) continue;
-    inb[k] = true;
-    const long long li = (long long)y * C.W + x;
-    gi[k] = C.off + li;
-    const DT D = dep[li];
-    const float c = cf[li];
-    float eh = __int_as_float(0x7fc00000), P[3] = {eh, eh, eh};
-    int nview = -1;
-    if (Depth<DT>::valid(D) && (!rig.use_conf || c > rig.tau)) {   // Eq. 9
-      const float z = Depth<DT>::z(D);
-      const float2 rx = rays[C.ray_x + x], ry = rays[C.ray_y + y];
-      world_point(C, z, rx.x, ry.x, P);                               // Eq. 8
-      float sh = 0.0f, sl = 0.0f, el = 0.0f;
-      nview = 0;
-      eh = 0.0f;
-      if (rig.use_cons && rig.k1 > 0) {
-        residual_sum<DT>(rig, C, rays, fp, z, rx, ry, sh, sl, nview);
-        fast_two_sum(sh, sl, sh, sl);
-        two_prod(sh, rig.einv_h, eh, el);                             // Eq. 7 exponent
-        el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
-        fast_two_sum(eh, el, eh, el);
-      }
-      // omega = C exp(-e) = mu 2^-m with e = m ln2 + f, f in [0, ln2): mu never underflows
-      int m = 0;
-      float fh = eh, fl = el;
-      if (eh > 0.0f) {
-        m = (int)floorf(__fmul_rn(fminf(eh, 1.0e9f), kInvLn2));
-        const float mf = (float)m;
-        float p, pe;
-        two_prod(mf, kLn2H, p, pe);
-        fh = __fsub_rn(eh, p);
-        fl = __fsub_rn(__fsub_rn(el, pe), __fmul_rn(mf, kLn2L));
-      }
-      const float base = rig.use_conf ? c : 1.0f;                     // Eq. 10
-      mu[k] = __fmul_rn(__fmul_rn(base, expf(-fh)), __fsub_rn(1.0f, fl));
-      mexp[k] = m;
-      rank[k] = ((unsigned long long)ordered(c) << 32) | (unsigned)(~(unsigned)gi[k]);
-      if (grid_coords(rig, P, r[k])) {
-        has[k] = true;
-        hc[k] = local_pos<TS>(s_ck, kKeyEmpty, coarse_key(r[k]));
-        if (hc[k] < 0) { has[k] = false; atomicOr(&t.cnt->error, kErrCoarseFull); }
-      }
+  for (int j = 0; j < 2; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i >= n_g) continue;
+    const int pid = s_pid[i];
+    const int x = tx * kTileW + (pid & (kTileW - 1)), y = ty * kTileH + pid / kTileW;
+    li[j] = (long long)y * W + x;
+    gi[j] = C.off + li[j];
+    const float z = Depth<DT>::z(dep[li[j]]);
+    const float c = cf[li[j]];
+    const float2 rx = __ldg(rays + C.ray_x + x), ry = __ldg(rays + C.ray_y + y);
+    float P[3];
+    world_point(C, z, rx.x, ry.x, P);                                 // Eq. 8
+    float sh = 0.0f, sl = 0.0f, eh = 0.0f, el = 0.0f;
+    int nview = 0;
+    if (rig.use_cons && k1 > 0) {
+      residual_sum<DT>(bc, k1, rays, fp, z, rx, ry, sh, sl, nview);
+      fast_two_sum(sh, sl, sh, sl);
+      two_prod(sh, rig.einv_h, eh, el);                               // Eq. 7 exponent
+      el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
+      fast_two_sum(eh, el, eh, el);
     }
+    // omega = C exp(-e) = mu 2^-m, e = m ln2 + f, f in [0, ln2): mu never underflows
+    int m = 0;
+    float fh = eh, fl = el;
+    if (eh > 0.0f) {
+      m = (int)floorf(__fmul_rn(fminf(eh, 1.0e9f), kInvLn2));
+      const float mf = (float)m;
+      float p, pe;
+      two_prod(mf, kLn2H, p, pe);
+      fh = __fsub_rn(eh, p);
+      fl = __fsub_rn(__fsub_rn(el, pe), __fmul_rn(mf, kLn2L));
+    }
+    const float base = rig.use_conf ? c : 1.0f;                       // Eq. 10
+    mu[j] = __fmul_rn(__fmul_rn(base, expf(-fh)), __fsub_rn(1.0f, fl));
+    mexp[j] = m;
+    cord[j] = ordered(c);
+    has[j] = grid_coords(rig, P, r[j]);
     if (trace) {
       if (tr.pw) {
-        tr.pw[3 * gi[k] + 0] = P[0] * unit_m;
-        tr.pw[3 * gi[k] + 1] = P[1] * unit_m;
-        tr.pw[3 * gi[k] + 2] = P[2] * unit_m;
+        tr.pw[3 * gi[j] + 0] = P[0] * unit_m;
+        tr.pw[3 * gi[j] + 1] = P[1] * unit_m;
+        tr.pw[3 * gi[j] + 2] = P[2] * unit_m;
       }
-      if (tr.e) tr.e[gi[k]] = eh;
-      if (tr.omega) tr.omega[gi[k]] = nview >= 0 ? ldexpf(mu[k], -mexp[k]) : __int_as_float(0x7fc00000);
-      if (tr.nview) tr.nview[gi[k]] = nview;
+      if (tr.e) tr.e[gi[j]] = eh;
+      if (tr.omega) tr.omega[gi[j]] = ldexpf(mu[j], -m);
+      if (tr.nview) tr.nview[gi[j]] = nview;
+      if (tr.key && !has[j]) tr.key[gi[j]] = kKeyEmpty;
+    }
+    if (has[j]) {
+      hpos[j] = local_pos<kAssignTS>(s_ck, kKeyEmpty, coarse_key(r[j]));
+      if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrCoarseFull); }
     }
   }
   __syncthreads();
-  // Sec. II.5(1)d: the level of each coarse cell present in the tile
-  for (int i = threadIdx.x; i < TS; i += kThreads) {
+  // (c) Sec. II.5(1)d: level of each coarse cell present in the tile
+  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
     const unsigned long long ck = s_ck[i];
-    if (ck == kKeyEmpty) continue;
-    s_cl[i] = (unsigned char)level_for(coarse_count_of(t, ck), rig.n_min, rig.max_level);
+    if (ck != kKeyEmpty)
+      s_cl[i] = (unsigned char)level_for(coarse_count_of(t, ck), rig.n_min, rig.max_level);
   }
   __syncthreads();
-  // Sec. II.5(1)e: cell key; block-local member count, representative, weight exponent
+  // (c) Sec. II.5(1)e: cell key and the point's offset inside its cell
+  float frac[2][3];
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    unsigned long long fk = kKeyEmpty;
-    if (has[k]) {
-      fk = fine_key(r[k], s_cl[hc[k]]);
-      hf[k] = local_pos<TS>(s_fk, kKeyEmpty, fk);
-      if (hf[k] >= 0) {
-        atomicAdd(&s_fcnt[hf[k]], 1u);
-        atomicMax(&s_frep[hf[k]], rank[k]);
-        atomicMin(&s_fmin[hf[k]], mexp[k]);
-      } else {
-        has[k] = false;
-        atomicOr(&t.cnt->error, kErrFineFull);
-      }
-    }
-    if (trace && tr.key && inb[k]) tr.key[gi[k]] = has[k] ? fk : kKeyEmpty;
+  for (int j = 0; j < 2; ++j) {
+    if (!has[j]) continue;
+    const int l = s_cl[hpos[j]];
+    const unsigned long long fk = fine_key(r[j], l);
+    const int kk[3] = {(int)((fk >> 40) & 0xfffff) - kKeyBias, (int)((fk >> 20) & 0xfffff) - kKeyBias,
+                       (int)(fk & 0xfffff) - kKeyBias};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) frac[j][a] = __fsub_rn(ldexpf(r[j][a], l), (float)kk[a]);
+    hpos[j] = local_pos<kAssignTS>(s_fk, kKeyEmpty, fk);
+    if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrFineFull); }
+    if (trace && tr.key) tr.key[gi[j]] = has[j] ? fk : kKeyEmpty;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < TS; i += kThreads) {
+  // compact the tile's cells: entry index per hash position
+  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
     const unsigned long long fk = s_fk[i];
     if (fk == kKeyEmpty) continue;
-    const unsigned slot = fine_insert(t, fk);
-    s_fslot[i] = slot;
-    if (slot != kSlotNone) {
-      atomicAdd(&t.meta[slot].count, s_fcnt[i]);
-      atomicMax(&t.meta[slot].rep, s_frep[i]);
-      atomicMin(&t.meta[slot].mmin, s_fmin[i]);
-    }
-  }
-  __syncthreads();
+    const int e = (int)atomicAdd(&s_n, 1u);
+    s_fi[i] = e;
+    s_ek[e] = fk;
+    s_cnt[e] = 0u;
+    s_cmax[e] = 0u;
+    s_gmin[e] = 0xffffffffu;
+    s_min[e] = INT_MAX;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (!inb[k]) continue;
-    Rec rc;
-    rc.slot = has[k] ? s_fslot[hf[k]] : kSlotNone;
-    rc.mu = mu[k];
-    rc.m = mexp[k];
-    t.rec[gi[k]] = rc;
+    for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
   }
-}
-
-// ------------------------------------------------------------------ accumulate step
-template <typename DT>
-__global__ void __launch_bounds__(kThreads)
-k_accum(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t) {
-  constexpr int TS = 2 * kTilePx;
-  constexpr int NL = kTilePx;
-  __shared__ unsigned s_hk[TS];
-  __shared__ int s_hi[TS];
-  __shared__ unsigned s_slot[NL];
-  __shared__ unsigned long long s_key[NL];
-  __shared__ unsigned s_repg[NL];
-  __shared__ int s_min[NL];
-  __shared__ unsigned long long s_acc[7][NL];
-  __shared__ unsigned s_n;
-  const RigDev& rig = *rigp;
-  const int cam = blockIdx.y;
-  const CamDev& C = rig.cam[cam];
-  const int tiles_x = (C.W + kTileW - 1) / kTileW;
-  const int tiles_y = (C.H + kTileH - 1) / kTileH;
-  if ((int)blockIdx.x >= tiles_x * tiles_y) return;
-  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < TS; i += kThreads) s_hk[i] = kSlotNone;
-  for (int i = threadIdx.x; i < NL; i += kThreads)
-    for (int a = 0; a < 7; ++a) s_acc[a][i] = 0ull;
-  if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-
-  const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
-  const uint8_t* __restrict__ col = fp.rgb[cam];
-  Rec rc[2];
-  int h[2] = {-1, -1};
-  int xs[2], ys[2];
-  long long gi[2];
+  // (d) Sec. II.5(2)a: members, largest C, smallest weight exponent
+  int ent[2] = {0, 0};
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    xs[k] = tx * kTileW + lane;
-    ys[k] = ty * kTileH + warp + 8 * k;
-    rc[k].slot = kSlotNone;
-    gi[k] = 0;
-    if (xs[k] >= C.W || ys[k] >= C.H) continue;
-    gi[k] = C.off + (long long)ys[k] * C.W + xs[k];
-    rc[k] = t.rec[gi[k]];
-    if (rc[k].slot != kSlotNone) h[k] = local_pos<TS>(s_hk, kSlotNone, rc[k].slot);
+  for (int j = 0; j < 2; ++j) {
+    if (!has[j]) continue;
+    ent[j] = s_fi[hpos[j]];
+    atomicAdd(&s_cnt[ent[j]], 1u);
+    atomicMax(&s_cmax[ent[j]], cord[j]);
+    atomicMin(&s_min[ent[j]], mexp[j]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < TS; i += kThreads) {
-    const unsigned slot = s_hk[i];
-    if (slot == kSlotNone) continue;
-    const int idx = (int)atomicAdd(&s_n, 1u);
-    s_hi[i] = idx;
-    s_slot[idx] = slot;
-    const SlotMeta m = t.meta[slot];
-    s_key[idx] = m.key;
-    s_repg[idx] = ~(unsigned)(m.rep & 0xffffffffull);
-    s_min[idx] = m.mmin;
-  }
-  __syncthreads();
+  // representative: lowest pixel index among the largest C; Eq. 11 sums at the tile's
+  // scale 2^-(36 + mmin_tile), each 64-bit term split in two native 32-bit atomics
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (h[k] < 0) continue;
-    const int idx = s_hi[h[k]];
-    const long long li = (long long)ys[k] * C.W + xs[k];
-    float P[3], r[3];
-    world_point(C, Depth<DT>::z(dep[li]), rays[C.ray_x + xs[k]].x, rays[C.ray_y + ys[k]].x, P);
-    grid_coords(rig, P, r);
-    const unsigned long long key = s_key[idx];
-    const int l = (int)(key >> 60);
-    const int kk[3] = {(int)((key >> 40) & 0xfffff) - kKeyBias, (int)((key >> 20) & 0xfffff) - kKeyBias,
-                       (int)(key & 0xfffff) - kKeyBias};
-    const int sh = rc[k].m - s_min[idx];
-    const float w = sh > 62 ? 0.0f : ldexpf(rc[k].mu, kFixShift - sh);
+  for (int j = 0; j < 2; ++j) {
+    if (!has[j]) continue;
+    const int e = ent[j];
+    if (cord[j] == s_cmax[e]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
+    const int sh = mexp[j] - s_min[e];
+    const float w = sh > 62 ? 0.0f : ldexpf(mu[j], kFixShift - sh);
+    const uint8_t* px = col + 3 * li[j];
     unsigned long long q[7];
     q[0] = __float2ull_rn(w);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float frac = __fsub_rn(ldexpf(r[a], l), (float)kk[a]);  // in [0, 1]
-      q[1 + a] = __float2ull_rn(__fmul_rn(w, frac));
-    }
-    const uint8_t* px = col + 3 * li;
+    for (int a = 0; a < 3; ++a) q[1 + a] = __float2ull_rn(__fmul_rn(w, frac[j][a]));
 #pragma unroll
     for (int a = 0; a < 3; ++a) q[4 + a] = __float2ull_rn(__fmul_rn(w, (float)px[a] * 0.00390625f));
 #pragma unroll
-    for (int a = 0; a < 7; ++a) atomicAdd(&s_acc[a][idx], q[a]);
-    if ((unsigned)gi[k] == s_repg[idx])
-      atomicOr(&t.bitmap[gi[k] >> 5], 1u << (gi[k] & 31));
+    for (int a = 0; a < 7; ++a) {
+      atomicAdd(&s_acc[(2 * a) * kAssignNL + e], (unsigned)(q[a] & ((1ull << kLoBits) - 1ull)));
+      atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], (unsigned)(q[a] >> kLoBits));
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < (int)s_n; i += kThreads) {
-    SlotAcc* A = &t.acc[s_slot[i]];
-    atomicAdd(&A->w, s_acc[0][i]);
-    atomicAdd(&A->x, s_acc[1][i]);
-    atomicAdd(&A->y, s_acc[2][i]);
-    atomicAdd(&A->z, s_acc[3][i]);
-    atomicAdd(&A->r, s_acc[4][i]);
-    atomicAdd(&A->g, s_acc[5][i]);
-    atomicAdd(&A->b, s_acc[6][i]);
+  // one partial record per (tile, cell), pushed onto the cell's list
+  const unsigned n_local = s_n;
+  if (threadIdx.x == 0) s_base = atomicAdd(&t.cnt->n_partials, n_local);
+  __syncthreads();
+  for (int e = threadIdx.x; e < (int)n_local; e += kThreads) {
+    const unsigned slot = fine_insert(t, s_ek[e]);
+    const unsigned pi = s_base + (unsigned)e;
+    if (slot == kSlotNone) continue;
+    if (pi >= t.max_partials) { atomicOr(&t.cnt->error, kErrPartials); continue; }
+    Partial p;
+    p.count = s_cnt[e];
+    p.mmin = s_min[e];
+    p.pad = 0u;
+    p.rep = ((unsigned long long)s_cmax[e] << 32) | (unsigned)(~s_gmin[e]);
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+      p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
+               s_acc[(2 * a) * kAssignNL + e];
+    p.next = atomicExch(&t.fhead[slot], pi);
+    t.part[pi] = p;
+  }
+}
+
+// ------------------------------------------------------------------ reduce step
+__global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
+  const unsigned n_cells = min(t.cnt->n_cells, t.fmask + 1u);
+  const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
+  const unsigned n_part = min(t.cnt->n_partials, t.max_partials);
+  const unsigned n = max(n_cells, n_coarse);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < n_cells) {
+      const unsigned slot = t.fused[i];
+      const unsigned long long key = t.fkey[slot];
+      const unsigned head = t.fhead[slot];
+      unsigned count = 0u, steps = 0u;
+      unsigned long long rep = 0ull;
+      int mmin = INT_MAX;
+      for (unsigned p = head; p != kSlotNone && steps <= n_part; p = t.part[p].next, ++steps) {
+        const Partial& P = t.part[p];
+        count += P.count;
+        rep = max(rep, P.rep);
+        mmin = min(mmin, P.mmin);
+      }
+      unsigned long long S[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+      steps = 0u;
+      for (unsigned p = head; p != kSlotNone && steps <= n_part; p = t.part[p].next, ++steps) {
+        const Partial& P = t.part[p];
+        const int sh = P.mmin - mmin;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) S[a] += sh < 64 ? (P.s[a] >> sh) : 0ull;
+      }
+      if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
+      const unsigned g = head != kSlotNone ? ~(unsigned)(rep & 0xffffffffull) : 0xffffffffu;
+      CellOut c;
+      const int l = (int)(key >> 60);
+      const double edge = ldexp(out.s0_m, -l);
+      const double kx = (double)((int)((key >> 40) & 0xfffff) - kKeyBias);
+      const double ky = (double)((int)((key >> 20) & 0xfffff) - kKeyBias);
+      const double kz = (double)((int)(key & 0xfffff) - kKeyBias);
+      const double Wq = (double)S[0];
+      const double inv = S[0] ? 1.0 / Wq : __longlong_as_double(0x7ff8000000000000ll);
+      c.pos[0] = (float)(edge * (kx + (double)S[1] * inv));
+      c.pos[1] = (float)(edge * (ky + (double)S[2] * inv));
+      c.pos[2] = (float)(edge * (kz + (double)S[3] * inv));
+      c.rgb[0] = (float)(256.0 * (double)S[4] * inv);
+      c.rgb[1] = (float)(256.0 * (double)S[5] * inv);
+      c.rgb[2] = (float)(256.0 * (double)S[6] * inv);
+      c.weight = (float)ldexp(Wq, -kFixShift - mmin);
+      c.count = count;
+      c.rep = g;
+      c.pad = 0u;
+      c.key = key;
+      t.staged[i] = c;
+      if (head != kSlotNone) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));
+      t.fkey[slot] = kKeyEmpty;                 // ready for the next frame
+      t.fhead[slot] = kSlotNone;
+    }
+    if (i < n_coarse) {
+      const unsigned cs = t.cused[i];
+      t.ckey[cs] = kKeyEmpty;
+      t.ccount[cs] = 0u;
+    }
   }
 }
 
@@ -666,6 +785,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Tables t, OutDev out) {
     const unsigned nc = t.cnt->n_cells;
     unsigned err = t.cnt->error;
     if ((long long)nc > out.max_cells) err |= kErrCells;
+    if (t.cnt->n_partials > t.max_partials) err |= kErrPartials;
     st.n_cells = (int64_t)(nc < out.max_cells ? nc : out.max_cells);
     for (int k = 0; k < 3; ++k) {
       st.bbox[k] = st.n_gated ? (float)((double)from_ordered(mn[k]) * out.unit_m) : __int_as_float(0x7f800000);
@@ -677,54 +797,28 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Tables t, OutDev out) {
   }
 }
 
-// ------------------------------------------------------------------ emit + clear
+// ------------------------------------------------------------------ emit
 __global__ void __launch_bounds__(kThreads) k_emit(Tables t, OutDev out) {
   const unsigned n_cells = min(t.cnt->n_cells, t.fmask + 1u);
-  const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
-  const unsigned n = max(n_cells, n_coarse);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i < n_cells) {
-      const unsigned slot = t.fused[i];
-      const SlotMeta m = t.meta[slot];
-      const SlotAcc A = t.acc[slot];
-      const unsigned g = ~(unsigned)(m.rep & 0xffffffffull);
-      const unsigned w = g >> 5;
-      const unsigned long long rnk = (unsigned long long)t.bsum[w >> 10] + t.wprefix[w] +
-                                     __popc(t.bitmap[w] & ((1u << (g & 31)) - 1u));
-      if (rnk < (unsigned long long)out.max_cells) {
-        const int l = (int)(m.key >> 60);
-        const double edge = ldexp(out.s0_m, -l);
-        const double kx = (double)((int)((m.key >> 40) & 0xfffff) - kKeyBias);
-        const double ky = (double)((int)((m.key >> 20) & 0xfffff) - kKeyBias);
-        const double kz = (double)((int)(m.key & 0xfffff) - kKeyBias);
-        const double W = (double)A.w;
-        const double inv = A.w ? 1.0 / W : __longlong_as_double(0x7ff8000000000000ll);
-        out.pos[3 * rnk + 0] = (float)(edge * (kx + (double)A.x * inv));
-        out.pos[3 * rnk + 1] = (float)(edge * (ky + (double)A.y * inv));
-        out.pos[3 * rnk + 2] = (float)(edge * (kz + (double)A.z * inv));
-        out.rgb[3 * rnk + 0] = (float)(256.0 * (double)A.r * inv);
-        out.rgb[3 * rnk + 1] = (float)(256.0 * (double)A.g * inv);
-        out.rgb[3 * rnk + 2] = (float)(256.0 * (double)A.b * inv);
-        out.weight[rnk] = (float)ldexp(W, -kFixShift - m.mmin);
-        out.count[rnk] = m.count;
-        out.rep[rnk] = g;
-        out.key[rnk] = m.key;
-      }
-      SlotMeta z;
-      z.key = kKeyEmpty;
-      z.rep = 0ull;
-      z.mmin = INT_MAX;
-      z.count = 0u;
-      z.pad = 0ull;
-      t.meta[slot] = z;
-      SlotAcc za = {};
-      t.acc[slot] = za;
-    }
-    if (i < n_coarse) {
-      const unsigned cs = t.cused[i];
-      t.ckey[cs] = kKeyEmpty;
-      t.ccount[cs] = 0u;
-    }
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
+    const CellOut c = t.staged[i];
+    const unsigned g = c.rep;
+    if ((long long)g >= t.n_words * 32) continue;          // cell without partials (overflow)
+    const unsigned w = g >> 5;
+    if (!((t.bitmap[w] >> (g & 31)) & 1u)) continue;
+    const unsigned long long rnk = (unsigned long long)t.bsum[w >> 10] + t.wprefix[w] +
+                                   __popc(t.bitmap[w] & ((1u << (g & 31)) - 1u));
+    if (rnk >= (unsigned long long)out.max_cells) continue;
+    out.pos[3 * rnk + 0] = c.pos[0];
+    out.pos[3 * rnk + 1] = c.pos[1];
+    out.pos[3 * rnk + 2] = c.pos[2];
+    out.rgb[3 * rnk + 0] = c.rgb[0];
+    out.rgb[3 * rnk + 1] = c.rgb[1];
+    out.rgb[3 * rnk + 2] = c.rgb[2];
+    out.weight[rnk] = c.weight;
+    out.count[rnk] = c.count;
+    out.rep[rnk] = g;
+    out.key[rnk] = c.key;
   }
 }
 
@@ -732,15 +826,8 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   const unsigned n = max(fcap, ccap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < fcap) {
-      SlotMeta z;
-      z.key = kKeyEmpty;
-      z.rep = 0ull;
-      z.mmin = INT_MAX;
-      z.count = 0u;
-      z.pad = 0ull;
-      t.meta[i] = z;
-      SlotAcc za = {};
-      t.acc[i] = za;
+      t.fkey[i] = kKeyEmpty;
+      t.fhead[i] = kSlotNone;
     }
     if (i < ccap) {
       t.ckey[i] = kKeyEmpty;
@@ -753,6 +840,13 @@ template <typename DT>
 cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
                          const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
                          cudaEvent_t* ev) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_assign<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kAssignSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
   cudaError_t err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
@@ -760,9 +854,10 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   mark(1);
   k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x);
   mark(2);
-  k_assign<DT><<<dim3(geo.tiles_max, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, tr, (float)out.unit_m);
+  k_assign<DT><<<dim3(geo.tiles_max, geo.n_cams), kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr,
+                                                                                (float)out.unit_m);
   mark(3);
-  k_accum<DT><<<dim3(geo.tiles_max, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t);
+  k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
   mark(4);
   k_scan_words<<<t.n_wblocks, 1024, 0, s>>>(t);
   k_scan_blocks<<<1, 1024, 0, s>>>(t, out);
