@@ -27,7 +27,7 @@ struct fuseflow_ctx {
   std::vector<int32_t> nbr;
   long long n_px = 0;
   long long max_cells = 0;
-  unsigned fcap = 0, ccap = 0;
+  unsigned max_slots = 0, ccap = 0;
   RigDev* d_rig = nullptr;
   float2* d_rays = nullptr;
   Tables tab{};
@@ -167,7 +167,7 @@ const char* fuseflow_status_string(int s) {
     case FUSEFLOW_OK: return "ok";
     case FUSEFLOW_ERR_INVALID_ARG: return "invalid argument";
     case FUSEFLOW_ERR_OUT_OF_MEMORY: return "out of memory";
-    case FUSEFLOW_ERR_CAPACITY: return "capacity exceeded (max_cells or hash table)";
+    case FUSEFLOW_ERR_CAPACITY: return "capacity exceeded (max_cells, cell slots or a table)";
     case FUSEFLOW_ERR_CUDA: return "CUDA runtime error";
     case FUSEFLOW_ERR_TIMEOUT: return "device wait timed out";
     case FUSEFLOW_ERR_INTERNAL: return "internal device check failed";
@@ -281,21 +281,32 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   }
   rig->n_px = off;
   ctx->n_px = off;
-  ctx->max_cells = params->max_cells > 0 ? params->max_cells : std::max<long long>(1024, (off + 1) / 2);
-  ctx->fcap = next_pow2((unsigned long long)std::max<long long>(2048, 2 * ctx->max_cells));
-  ctx->ccap = ctx->fcap;
+  ctx->max_cells = params->max_cells > 0 ? params->max_cells : std::max<long long>(65536, off / 8);
+  // A coarse cell at level l >= 1 holds n_c >= n_min 4^l points, so its 8^l dense slots are
+  // at most 2^Lmax n_c / n_min; level-0 coarse cells need one slot each.
+  const long long slot_bound = off + (((long long)1 << params->max_level) * off) / params->n_min;
+  ctx->max_slots = (unsigned)std::max<long long>(4096, std::min<long long>(slot_bound, 1ll << 26));
+  ctx->ccap = next_pow2((unsigned long long)std::max<long long>(4096, 2 * ctx->max_cells));
 
   // ---------------------------------------------------------------- launch geometry
   ctx->geo.n_cams = n_cams;
   ctx->geo.depth_f32 = rig->depth_f32;
-  ctx->geo.count_blocks_x = (int)((max_px + 1023) / 1024);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  {
+    // several 1024-pixel chunks per count block: about two waves of 4 blocks per SM
+    long long total_chunks = 0;
+    for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 1023) / 1024;
+    const long long per = total_chunks / (2ll * 4 * sms);
+    ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
+    const long long max_chunks = (max_px + 1023) / 1024;
+    ctx->geo.count_blocks_x = (int)((max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
+  }
   int tiles_max = 0;
   for (int i = 0; i < n_cams; ++i)
     tiles_max = std::max(tiles_max, ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16));
   ctx->geo.tiles_max = tiles_max;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  ctx->geo.emit_blocks = std::max(1, sms * 4);
+  ctx->geo.emit_blocks = std::max(1, sms * 8);
 
   // ---------------------------------------------------------------- device memory
   int status = FUSEFLOW_OK;
@@ -306,16 +317,20 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   auto take = [&](size_t bytes, size_t align) { o = align_up(o, align); size_t at = o; o += bytes; return at; };
   // (tile, cell) partials: at most one per gated pixel
   const unsigned max_partials = (unsigned)std::min<long long>(off, 0xfffffffell);
-  const size_t o_fkey = take(sizeof(unsigned long long) * ctx->fcap, 256);
-  const size_t o_fhead = take(sizeof(unsigned) * ctx->fcap, 256);
-  const size_t o_fused = take(sizeof(unsigned) * ctx->fcap, 256);
+  const size_t o_fkey = take(sizeof(unsigned long long) * ctx->max_slots, 256);
+  const size_t o_fhead = take(sizeof(unsigned) * ctx->max_slots, 256);
+  const size_t o_fmmin = take(sizeof(int) * ctx->max_slots, 256);
+  const size_t o_fused = take(sizeof(unsigned) * ctx->max_slots, 256);
   const size_t o_ckey = take(sizeof(unsigned long long) * ctx->ccap, 256);
   const size_t o_ccnt = take(sizeof(unsigned) * ctx->ccap, 256);
+  const size_t o_clev = take(sizeof(unsigned) * ctx->ccap, 256);
+  const size_t o_cbase = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
   const size_t o_part = take(sizeof(Partial) * (size_t)max_partials, 256);
-  const size_t o_staged = take(sizeof(CellOut) * ctx->fcap, 256);
+  const size_t o_pnext = take(sizeof(unsigned) * (size_t)max_partials, 256);
+  const size_t o_staged = take(sizeof(CellOut) * (size_t)ctx->max_cells, 256);
   const size_t o_wpre = take(sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bsum = take(sizeof(unsigned) * (size_t)n_wblocks, 256);
   ctx->table_bytes = o;
@@ -341,10 +356,15 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     Tables& t = ctx->tab;
     t.fkey = reinterpret_cast<unsigned long long*>(b + o_fkey);
     t.fhead = reinterpret_cast<unsigned*>(b + o_fhead);
+    t.fmmin = reinterpret_cast<int*>(b + o_fmmin);
     t.fused = reinterpret_cast<unsigned*>(b + o_fused);
-    t.fmask = ctx->fcap - 1;
+    t.max_slots = ctx->max_slots;
     t.ckey = reinterpret_cast<unsigned long long*>(b + o_ckey);
     t.ccount = reinterpret_cast<unsigned*>(b + o_ccnt);
+    t.clevel = reinterpret_cast<unsigned*>(b + o_clev);
+    t.cbase = reinterpret_cast<unsigned*>(b + o_cbase);
+    t.n_min = params->n_min;
+    t.max_level = params->max_level;
     t.cused = reinterpret_cast<unsigned*>(b + o_cused);
     t.cmask = ctx->ccap - 1;
     t.cnt = reinterpret_cast<FrameCounters*>(b + o_cnt);
@@ -352,6 +372,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     t.bstats = reinterpret_cast<BlockStats*>(b + o_bst);
     t.n_bstats = n_bstats;
     t.part = reinterpret_cast<Partial*>(b + o_part);
+    t.pnext = reinterpret_cast<unsigned*>(b + o_pnext);
     t.max_partials = max_partials;
     t.staged = reinterpret_cast<CellOut*>(b + o_staged);
     t.wprefix = reinterpret_cast<unsigned*>(b + o_wpre);
@@ -374,7 +395,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
         cudaMemcpy(ctx->d_rays, rays.data(), sizeof(float2) * rays.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->d_tables, 0, ctx->table_bytes) != cudaSuccess ||
         cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
-        launch_init_tables(t, ctx->fcap, ctx->ccap, 0) != cudaSuccess ||
+        launch_init_tables(t, ctx->max_slots, ctx->ccap, 0) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
       status = FUSEFLOW_ERR_CUDA;
   }
@@ -437,7 +458,7 @@ int fuseflow_read_stats(fuseflow_ctx* ctx, fuseflow_stats* host_stats, void* str
       cudaStreamSynchronize(s) != cudaSuccess)
     return FUSEFLOW_ERR_CUDA;
   const unsigned err = (unsigned)host_stats->error;
-  if (err & (kErrFineFull | kErrCoarseFull | kErrCells)) return FUSEFLOW_ERR_CAPACITY;
+  if (err & (kErrSlots | kErrCoarseFull | kErrCells)) return FUSEFLOW_ERR_CAPACITY;
   if (err & kErrPartials) return FUSEFLOW_ERR_CAPACITY;
   if (err & (kErrCoarseMiss | kErrList)) return FUSEFLOW_ERR_INTERNAL;
   return FUSEFLOW_OK;
@@ -551,8 +572,8 @@ int fuseflow_read_stage_times(fuseflow_ctx* ctx, double* ms, int64_t* n_frames) 
 }
 
 const char* fuseflow_stage_name(int stage) {
-  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "reduce", "scan",
-                                                 "emit"};
+  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "link", "reduce",
+                                                 "scan", "emit"};
   return (stage >= 0 && stage < FUSEFLOW_N_STAGES) ? names[stage] : "unknown";
 }
 
@@ -568,7 +589,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
 // Allocation-free variant of fuseflow_fuse_frame.
 //
 // All scratch (rig constants, ray tables, hash tables, per-pixel records, scan buffers)
-// lives in one file-scope device array of kStaticBytes (about 17 MiB), held by every GPU
+// lives in one file-scope device array of kStaticBytes (about 21 MiB), held by every GPU
 // that loads this library until the process exits.  Host code never dereferences the
 // array's name: the device address comes from cudaGetSymbolAddress, taken once per device
 // on that device's first call (which also clears the hash tables and synchronizes the
@@ -580,11 +601,12 @@ namespace {
 constexpr long long kStaticMaxPixels = 1ll << 19;      // 524,288 pixels per frame
 constexpr unsigned kStaticMaxPartials = 1u << 17;      // (tile, cell) partial records
 constexpr long long kStaticMaxCells = 1ll << 15;       // 32,768 output cells
-constexpr unsigned kStaticSlots = 1u << 16;            // fine and coarse hash slots
+constexpr unsigned kStaticSlots = 1u << 18;            // dense cell slots
+constexpr unsigned kStaticCoarse = 1u << 16;           // coarse hash slots
 constexpr int kStaticMaxRays = 1 << 16;                // sum over cameras of W + H
 constexpr long long kStaticWords = kStaticMaxPixels / 32;
 constexpr int kStaticWBlocks = (int)((kStaticWords + 1023) / 1024);
-constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 1024 + 1);
+constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 1024 + 1);   // chunks = 1
 constexpr int kStaticMaxDevices = 64;
 
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
@@ -592,18 +614,22 @@ constexpr size_t kSRig = 0;
 constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
 constexpr size_t kSFKey = al256(kSRays + sizeof(float2) * kStaticMaxRays);
 constexpr size_t kSFHead = al256(kSFKey + sizeof(unsigned long long) * kStaticSlots);
-constexpr size_t kSFused = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSFMmin = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSFused = al256(kSFMmin + sizeof(int) * kStaticSlots);
 constexpr size_t kSCKey = al256(kSFused + sizeof(unsigned) * kStaticSlots);
-constexpr size_t kSCCount = al256(kSCKey + sizeof(unsigned long long) * kStaticSlots);
-constexpr size_t kSCUsed = al256(kSCCount + sizeof(unsigned) * kStaticSlots);
-constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSCCount = al256(kSCKey + sizeof(unsigned long long) * kStaticCoarse);
+constexpr size_t kSCLev = al256(kSCCount + sizeof(unsigned) * kStaticCoarse);
+constexpr size_t kSCBase = al256(kSCLev + sizeof(unsigned) * kStaticCoarse);
+constexpr size_t kSCUsed = al256(kSCBase + sizeof(unsigned) * kStaticCoarse);
+constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticCoarse);
 constexpr size_t kSBStats = al256(kSCnt + sizeof(FrameCounters) + sizeof(unsigned) * kStaticWords);
 constexpr size_t kSPart = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
-constexpr size_t kSStaged = al256(kSPart + sizeof(Partial) * kStaticMaxPartials);
-constexpr size_t kSWPre = al256(kSStaged + sizeof(CellOut) * kStaticSlots);
+constexpr size_t kSPNext = al256(kSPart + sizeof(Partial) * kStaticMaxPartials);
+constexpr size_t kSStaged = al256(kSPNext + sizeof(unsigned) * kStaticMaxPartials);
+constexpr size_t kSWPre = al256(kSStaged + sizeof(CellOut) * kStaticMaxCells);
 constexpr size_t kSBSum = al256(kSWPre + sizeof(unsigned) * kStaticWords);
 constexpr size_t kStaticBytes = al256(kSBSum + sizeof(unsigned) * kStaticWBlocks);
-static_assert(kStaticBytes <= (18u << 20), "static scratch must stay modest");
+static_assert(kStaticBytes <= (24u << 20), "static scratch must stay modest");
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -651,17 +677,21 @@ Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   Tables t{};
   t.fkey = reinterpret_cast<unsigned long long*>(base + kSFKey);
   t.fhead = reinterpret_cast<unsigned*>(base + kSFHead);
+  t.fmmin = reinterpret_cast<int*>(base + kSFMmin);
   t.fused = reinterpret_cast<unsigned*>(base + kSFused);
-  t.fmask = kStaticSlots - 1;
+  t.max_slots = kStaticSlots;
   t.ckey = reinterpret_cast<unsigned long long*>(base + kSCKey);
   t.ccount = reinterpret_cast<unsigned*>(base + kSCCount);
+  t.clevel = reinterpret_cast<unsigned*>(base + kSCLev);
+  t.cbase = reinterpret_cast<unsigned*>(base + kSCBase);
   t.cused = reinterpret_cast<unsigned*>(base + kSCUsed);
-  t.cmask = kStaticSlots - 1;
+  t.cmask = kStaticCoarse - 1;
   t.cnt = reinterpret_cast<FrameCounters*>(base + kSCnt);
   t.bitmap = reinterpret_cast<unsigned*>(t.cnt + 1);
   t.bstats = reinterpret_cast<BlockStats*>(base + kSBStats);
   t.n_bstats = n_bstats;
   t.part = reinterpret_cast<Partial*>(base + kSPart);
+  t.pnext = reinterpret_cast<unsigned*>(base + kSPNext);
   t.max_partials = kStaticMaxPartials;
   t.staged = reinterpret_cast<CellOut*>(base + kSStaged);
   t.wprefix = reinterpret_cast<unsigned*>(base + kSWPre);
@@ -680,7 +710,7 @@ int static_scratch(int dev, cudaStream_t s, unsigned char** out) {
     if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return FUSEFLOW_ERR_CUDA;
     unsigned char* base = static_cast<unsigned char*>(p);
     const Tables t = static_tables(base, kStaticMaxPixels, kStaticBStats);
-    if (launch_init_tables(t, kStaticSlots, kStaticSlots, s) != cudaSuccess ||
+    if (launch_init_tables(t, kStaticSlots, kStaticCoarse, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return FUSEFLOW_ERR_CUDA;
     g_static_dev[dev] = base;
@@ -799,11 +829,14 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   geo.n_cams = n_cams;
   geo.depth_f32 = rig.depth_f32;
   geo.count_blocks_x = (int)((max_px + 1023) / 1024);
+  geo.count_chunks = 1;
   geo.tiles_max = tiles_max;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  geo.emit_blocks = std::max(1, sms * 4);
-  const Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
+  geo.emit_blocks = std::max(1, sms * 8);
+  Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
+  t.n_min = params->n_min;
+  t.max_level = params->max_level;
   OutDev od{};
   od.stats = stats;
   od.pos = pos;

@@ -26,7 +26,7 @@ constexpr float kTieBandPx = 4e-3f;      // float32 projection error bound (pixe
 constexpr float kZGuard = 1.0f;          // |a_z| below one depth unit: use the ff value
 
 // error bits of FrameCounters::error
-constexpr unsigned kErrFineFull = 1u;    // fine hash table could not take a key
+constexpr unsigned kErrSlots = 1u;       // the cells' dense slot ranges exceed the slot capacity
 constexpr unsigned kErrCoarseFull = 2u;  // coarse hash table could not take a key
 constexpr unsigned kErrCells = 4u;       // more cells than the output capacity
 constexpr unsigned kErrCoarseMiss = 8u;  // a point's coarse cell was not found (internal)
@@ -67,11 +67,12 @@ struct RigDev {
   PairDev pair[kMaxCams * kMaxK1];
 };
 
-// Per (tile, cell) partial result of the assign step, linked into its cell's list.
-// Sums are exact integers in units of 2^-(kFixShift + mmin) of the tile's own smallest
-// weight exponent mmin; the reduce step shifts them to the cell's smallest exponent.
+// Per (tile, cell) partial result of the assign step; the link step pushes it onto its
+// cell's list (next[] holds the links).  Sums are exact integers in units of
+// 2^-(kFixShift + mmin) of the tile's own smallest weight exponent mmin; the reduce step
+// shifts them to the cell's smallest exponent.
 struct __align__(16) Partial {
-  unsigned next;                 // next partial of the same cell, or kSlotNone
+  unsigned slot;                 // dense slot of the cell
   unsigned count;                // members in the tile
   int mmin;                      // smallest weight exponent m in the tile
   unsigned pad;
@@ -92,10 +93,17 @@ struct __align__(16) CellOut {
 };
 static_assert(sizeof(CellOut) == 48, "staged cell layout");
 
-struct FrameCounters {
+struct FrameCounters {           // zeroed before every frame
   unsigned n_cells, n_coarse;
   unsigned error;
   unsigned n_partials;
+  unsigned long long n_valid, n_gated, n_oor;
+  unsigned bmin_inv[3];          // ~ordered(min): max-reduced so that zero is neutral
+  unsigned bmax[3];              // ordered(max)
+  unsigned scan_done;            // blocks of the scan step that have finished
+  unsigned count_done;           // blocks of the count step that have finished
+  unsigned n_slots;              // dense cell slots in use (sum over coarse cells of 8^l)
+  unsigned pad;
 };
 
 struct BlockStats {              // per block of the coarse-count step
@@ -193,15 +201,20 @@ __device__ __forceinline__ void world_point(const CamDev& c, float z, float rx, 
                      __fmaf_rn(c.Rwc[3 * k + 1], py, __fmaf_rn(c.Rwc[3 * k + 2], z, c.cwc[k])));
 }
 
-// Sec. II.5(1): coarse-grid coordinate r = P / s0 and the range test at the finest level.
+// 2^e as a float for -126 <= e <= 127, built from its bits (exact scaling by a product).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// Sec. II.5(1): coarse-grid coordinate r = P / s0 and the range test at the finest level:
+// floor(r 2^Lmax) in [-2^19, 2^19)  <=>  r 2^Lmax in [-2^19, 2^19).
 __device__ __forceinline__ bool grid_coords(const RigDev& rig, const float P[3], float r[3]) {
   bool ok = true;
   const float lim = (float)kKeyBias;
+  const float sL = pow2f(rig.max_level);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     r[k] = __fmul_rn(P[k], rig.inv_s0u);
-    const float f = floorf(ldexpf(r[k], rig.max_level));
-    ok = ok && (f >= -lim) && (f < lim);
+    const float v = __fmul_rn(r[k], sL);
+    ok = ok && (v >= -lim) && (v < lim);
   }
   return ok;
 }
@@ -220,8 +233,9 @@ __device__ __forceinline__ int level_for(unsigned n_c, int n_min, int max_level)
 }
 
 __device__ __forceinline__ unsigned long long fine_key(const float r[3], int l) {
-  return pack_key(l, (int)floorf(ldexpf(r[0], l)), (int)floorf(ldexpf(r[1], l)),
-                  (int)floorf(ldexpf(r[2], l)));
+  const float sl = pow2f(l);
+  return pack_key(l, (int)floorf(__fmul_rn(r[0], sl)), (int)floorf(__fmul_rn(r[1], sl)),
+                  (int)floorf(__fmul_rn(r[2], sl)));
 }
 
 }  // namespace ffl

@@ -16,25 +16,32 @@ struct FramePtrs {               // one frame's caller-owned device images, per 
 };
 
 struct Tables {                  // context-owned device scratch
-  unsigned long long* fkey;      // fine hash table keys, fcap entries
-  unsigned* fhead;               // first partial of each fine cell, kSlotNone if none
-  unsigned* fused;               // used fine slots, in insertion order
-  unsigned fmask;                // fcap - 1
-  unsigned long long* ckey;      // coarse hash table, ccap entries
+  // cells: dense slots, coarse cell c owns [cbase(c), cbase(c) + 8^level(c))
+  unsigned long long* fkey;      // key of each used slot, max_slots entries
+  unsigned* fhead;               // first partial of each slot, kSlotNone if none
+  int* fmmin;                    // smallest weight exponent of each slot
+  unsigned* fused;               // used slots, in claim order
+  unsigned max_slots;
+  // coarse hash table (open addressing), ccap entries
+  unsigned long long* ckey;
   unsigned* ccount;
+  unsigned* clevel;              // refinement level of the coarse cell
+  unsigned* cbase;               // first dense slot of the coarse cell
   unsigned* cused;
   unsigned cmask;
   FrameCounters* cnt;
   BlockStats* bstats;            // one per block of the coarse-count step
   int n_bstats;
   Partial* part;                 // (tile, cell) partials, max_partials entries
+  unsigned* pnext;               // list link of each partial, max_partials entries
   unsigned max_partials;
-  CellOut* staged;               // fused cells by insertion order, fcap entries
+  CellOut* staged;               // fused cells by claim order, max_cells entries
   unsigned* bitmap;              // representative bitmap, one bit per pixel
   unsigned* wprefix;             // per-word exclusive prefix within its 1024-word block
   unsigned* bsum;                // per 1024-word block: exclusive prefix after the scan
   long long n_words;
   int n_wblocks;
+  int n_min, max_level;          // level rule (Sec. II.5(1)d)
 };
 
 struct TraceDev {
@@ -62,6 +69,7 @@ struct Geometry {
   int n_cams;
   int depth_f32;
   int count_blocks_x;            // blocks per camera of the coarse-count step (max over cams)
+  int count_chunks;              // 1024-pixel chunks per block of the coarse-count step
   int tiles_max;                 // 32x16 tiles per camera (max over cams)
   int emit_blocks;
 };

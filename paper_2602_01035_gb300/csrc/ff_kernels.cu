@@ -8,11 +8,12 @@
 //            (c) level per coarse cell (Sec. II.5(1)d), cell key (Sec. II.5(1)e), fine
 //            hash insertion; (d) per (tile, cell): member count, representative
 //            (Sec. II.5(2)a), smallest weight exponent and exact fixed-point sums of
-//            omega, omega P, omega RGB (Eq. 11), written as one partial record linked
-//            into the cell's list
+//            omega, omega P, omega RGB (Eq. 11), written as one partial record
+//   link     per partial: push it onto its cell's list (cells own dense slots: coarse
+//            cell c owns 8^level(c) consecutive slots, sized by the count step's last block)
 //   reduce   per cell: walk its partials, combine them, stage the fused cell, mark its
 //            representative; the used hash slots are cleared for the next frame
-//   scan     ranks of the representatives (output order), frame statistics
+//   scan     ranks of the representatives (output order) and frame statistics, one kernel
 //   emit     fused cells in representative order
 //
 // Every reduction is order-independent (integer counts, max, min and fixed-point sums,
@@ -38,26 +39,6 @@ constexpr float kLn2L = -1.904654299957768e-09f;          // ln 2 - kLn2H
 constexpr float kInvLn2 = 1.44269504088896340736f;
 
 // ------------------------------------------------------------------ global hash tables
-__device__ __forceinline__ unsigned fine_insert(const Tables& t, unsigned long long key) {
-  unsigned h = (unsigned)mix64(key) & t.fmask;
-  for (int probe = 0; probe < kMaxProbe; ++probe) {
-    unsigned long long cur = __ldcg(&t.fkey[h]);
-    if (cur == key) return h;
-    if (cur == kKeyEmpty) {
-      cur = atomicCAS(&t.fkey[h], kKeyEmpty, key);
-      if (cur == kKeyEmpty) {
-        const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
-        if (n <= t.fmask) t.fused[n] = h;
-        return h;
-      }
-      if (cur == key) return h;
-    }
-    h = (h + 1) & t.fmask;
-  }
-  atomicOr(&t.cnt->error, kErrFineFull);
-  return kSlotNone;
-}
-
 __device__ __forceinline__ unsigned coarse_insert(const Tables& t, unsigned long long key) {
   unsigned h = (unsigned)mix64(key) & t.cmask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
@@ -78,23 +59,81 @@ __device__ __forceinline__ unsigned coarse_insert(const Tables& t, unsigned long
   return kSlotNone;
 }
 
-__device__ __forceinline__ unsigned coarse_count_of(const Tables& t, unsigned long long key) {
+// Coarse hash slot of an existing coarse key (inserted by the count step).
+__device__ __forceinline__ unsigned coarse_find(const Tables& t, unsigned long long key) {
   unsigned h = (unsigned)mix64(key) & t.cmask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
     const unsigned long long cur = __ldcg(&t.ckey[h]);
-    if (cur == key) return __ldcg(&t.ccount[h]);
+    if (cur == key) return h;
     if (cur == kKeyEmpty) break;
     h = (h + 1) & t.cmask;
   }
   atomicOr(&t.cnt->error, kErrCoarseMiss);
-  return 0;
+  return kSlotNone;
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* s_w, T& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < NT / 32 ? s_w[lane] : (T)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) s_w[lane] = w;
+  }
+  __syncthreads();
+  total = s_w[NT / 32 - 1];
+  const T before = warp ? s_w[warp - 1] : (T)0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// Sec. II.5(1)d for every coarse cell once all counts are in: level l and the first of
+// its 8^l dense cell slots (exclusive prefix over the coarse cells in claim order).
+__device__ void assign_levels(Tables& t) {
+  __shared__ unsigned long long s_w[kThreads / 32];
+  const unsigned n_coarse = min(__ldcg(&t.cnt->n_coarse), t.cmask + 1u);
+  unsigned long long carry = 0;
+  for (unsigned base = 0; base < n_coarse; base += kThreads) {
+    const unsigned i = base + threadIdx.x;
+    unsigned cs = 0, l = 0;
+    unsigned long long size = 0;
+    if (i < n_coarse) {
+      cs = __ldcg(&t.cused[i]);
+      l = (unsigned)level_for(__ldcg(&t.ccount[cs]), t.n_min, t.max_level);
+      size = 1ull << (3 * l);                  // 8^l <= 2^42
+    }
+    unsigned long long total;
+    const unsigned long long ex = block_excl_scan<kThreads, unsigned long long>(size, s_w, total);
+    if (i < n_coarse) {
+      const unsigned long long b = carry + ex;
+      t.clevel[cs] = l;
+      t.cbase[cs] = b + size <= t.max_slots ? (unsigned)b : kSlotNone;
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    t.cnt->n_slots = (unsigned)min(carry, (unsigned long long)t.max_slots);
+    if (carry > t.max_slots) atomicOr(&t.cnt->error, kErrSlots);
+  }
 }
 
 // Block-local open addressing (shared memory); returns the table position or -1.
 template <int TS, typename K>
-__device__ __forceinline__ int local_pos(K* tab, K empty, K key) {
+__device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe = TS) {
   unsigned h = (unsigned)mix64((unsigned long long)key) & (TS - 1);
-  for (int probe = 0; probe < TS; ++probe) {
+  for (int probe = 0; probe < max_probe; ++probe) {
     const K cur = *static_cast<volatile K*>(&tab[h]);
     if (cur == key) return (int)h;
     if (cur == empty) {
@@ -173,9 +212,10 @@ __device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1,
       a[1] = ah[1];
       a[2] = ah[2];
     }
-    const float inv = __frcp_rn(a[2]);
-    const float fu = __fadd_rn(__fmaf_rn(J.fx, __fmul_rn(a[0], inv), J.cx), 0.5f);
-    const float fv = __fadd_rn(__fmaf_rn(J.fy, __fmul_rn(a[1], inv), J.cy), 0.5f);
+    // float32 estimate of u + 1/2 (error well below kTieBandPx; near ties the pixel is
+    // decided exactly below)
+    const float fu = __fadd_rn(__fmaf_rn(J.fx, __fdividef(a[0], a[2]), J.cx), 0.5f);
+    const float fv = __fadd_rn(__fmaf_rn(J.fy, __fdividef(a[1], a[2]), J.cy), 0.5f);
     if (!(fu > -1.0f && fu < (float)J.W + 1.0f && fv > -1.0f && fv < (float)J.H + 1.0f))
       continue;
     const float ru = rintf(fu), rv = rintf(fv);
@@ -260,7 +300,7 @@ __device__ __forceinline__ void load4(const DT* __restrict__ d, const float* __r
 template <typename DT>
 __global__ void __launch_bounds__(kThreads, 4)
 k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
-        int blocks_x) {
+        int blocks_x, int chunks) {
   constexpr int TS = 2 * kCountBlockPx;
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
@@ -270,39 +310,43 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   const CamDev& C = rig.cam[cam];
   const long long npx = (long long)C.W * C.H;
   const int bid = cam * blocks_x + blockIdx.x;
-  if ((long long)blockIdx.x * kCountBlockPx >= npx) {
-    if (threadIdx.x == 0) {
-      BlockStats b = {};
-      for (int k = 0; k < 3; ++k) { b.bmin[k] = 0xffffffffu; b.bmax[k] = 0u; }
-      t.bstats[bid] = b;
-    }
-    return;
-  }
+  __shared__ bool s_last;
+  const long long c0 = (long long)blockIdx.x * chunks;          // first 1024-pixel chunk
+  const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
   __syncthreads();
 
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
-  const long long p0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * kCountPx;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  DT dv[4];
-  float cv[4];
   unsigned nv = 0, ng = 0, noor = 0;
   unsigned bmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, bmax[3] = {0u, 0u, 0u};
-  unsigned long long rk[kCountPx] = {kKeyEmpty, kKeyEmpty, kKeyEmpty, kKeyEmpty};
-  unsigned rn[kCountPx] = {1u, 1u, 1u, 1u};
-  if (p0 < npx) {
-    load4<DT>(dep, cf, p0, npx, dv, cv);
-    int y = (int)(p0 / C.W);
-    int x = (int)(p0 - (long long)y * C.W);
+  DT dv[4];
+  float cv[4];
+  long long pn = (c0 * kThreads + threadIdx.x) * kCountPx;
+  if (!idle && pn < npx) load4<DT>(dep, cf, pn, npx, dv, cv);
+  for (int ch = 0; ch < (idle ? 0 : chunks); ++ch) {
+    const long long pc = pn;
+    if ((c0 + ch) * kCountBlockPx >= npx) break;                 // uniform over the block
+    DT dcur[4];
+    float ccur[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { dcur[k] = dv[k]; ccur[k] = cv[k]; }
+    pn = pc + kCountBlockPx;                                      // prefetch the next chunk
+    if (ch + 1 < chunks && pn < npx) load4<DT>(dep, cf, pn, npx, dv, cv);
+    if (pc >= npx) continue;
+    unsigned long long rk[kCountPx] = {kKeyEmpty, kKeyEmpty, kKeyEmpty, kKeyEmpty};
+    unsigned rn[kCountPx] = {1u, 1u, 1u, 1u};
+    int y = (int)((unsigned)pc / (unsigned)C.W);                  // W H <= 2^30
+    int x = (int)((unsigned)pc - (unsigned)y * (unsigned)C.W);
 #pragma unroll
     for (int k = 0; k < kCountPx; ++k) {
-      if (p0 + k < npx && Depth<DT>::valid(dv[k])) {
+      if (pc + k < npx && Depth<DT>::valid(dcur[k])) {
         ++nv;
-        if (!rig.use_conf || cv[k] > rig.tau) {       // Eq. 9
+        if (!rig.use_conf || ccur[k] > rig.tau) {                 // Eq. 9
           ++ng;
           float P[3], r[3];
-          world_point(C, Depth<DT>::z(dv[k]), __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
+          world_point(C, Depth<DT>::z(dcur[k]), __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const unsigned o = ordered(P[a]);
@@ -315,33 +359,40 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
       }
       if (++x == C.W) { x = 0; ++y; }
     }
-  }
-  // Sec. II.5(1)c density estimate: merge the thread's equal neighbours, then one
-  // shared-memory update per distinct key and thread
+    // Sec. II.5(1)c density estimate: merge the thread's equal neighbours, then one
+    // shared-memory update per distinct key (global if the block table is full)
 #pragma unroll
-  for (int k = 1; k < kCountPx; ++k)
-    if (rk[k] != kKeyEmpty && rk[k] == rk[k - 1]) {
-      rn[k] += rn[k - 1];
-      rk[k - 1] = kKeyEmpty;
+    for (int k = 1; k < kCountPx; ++k)
+      if (rk[k] != kKeyEmpty && rk[k] == rk[k - 1]) {
+        rn[k] += rn[k - 1];
+        rk[k - 1] = kKeyEmpty;
+      }
+#pragma unroll
+    for (int j = 0; j < kCountPx; ++j) {
+      if (rk[j] == kKeyEmpty) continue;
+      const int h = local_pos<TS>(s_key, kKeyEmpty, rk[j], 64);
+      if (h >= 0) {
+        atomicAdd(&s_cnt[h], rn[j]);
+      } else {
+        const unsigned slot = coarse_insert(t, rk[j]);
+        if (slot != kSlotNone) atomicAdd(&t.ccount[slot], rn[j]);
+      }
     }
-#pragma unroll
-  for (int j = 0; j < kCountPx; ++j) {
-    if (rk[j] == kKeyEmpty) continue;
-    const int h = local_pos<TS>(s_key, kKeyEmpty, rk[j]);
-    if (h >= 0) atomicAdd(&s_cnt[h], rn[j]);
-    else atomicOr(&t.cnt->error, kErrCoarseFull);
   }
   // per-block pixel counts and extent
   unsigned vals[9] = {nv, ng, noor, bmin[0], bmin[1], bmin[2], bmax[0], bmax[1], bmax[2]};
   vals[0] = __reduce_add_sync(0xffffffffu, vals[0]);
   vals[1] = __reduce_add_sync(0xffffffffu, vals[1]);
   vals[2] = __reduce_add_sync(0xffffffffu, vals[2]);
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     vals[3 + a] = __reduce_min_sync(0xffffffffu, vals[3 + a]);
     vals[6 + a] = __reduce_max_sync(0xffffffffu, vals[6 + a]);
   }
-  if (lane == 0)
+  if (lane == 0) {
+#pragma unroll
     for (int a = 0; a < 9; ++a) s_red[warp][a] = vals[a];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     BlockStats b = {};
@@ -363,25 +414,41 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     const unsigned slot = coarse_insert(t, key);
     if (slot != kSlotNone) atomicAdd(&t.ccount[slot], s_cnt[i]);
   }
+  // the last block to finish (fenced counter, no waiting) sizes the cells' slot ranges
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    s_last = atomicAdd(&t.cnt->count_done, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    assign_levels(t);
+  }
 }
 
 // ------------------------------------------------------------------ assign step
 constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
+constexpr int kAssignCS = kTilePx;         // coarse-key positions (coarse keys <= pixels)
 constexpr int kAssignNL = kTilePx;         // distinct fine cells of a tile, at most
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 constexpr size_t kSmBC = 0;
-constexpr size_t kSmCK = align16(kSmBC + sizeof(BlockConst));      // u64[TS] coarse keys
-constexpr size_t kSmCL = align16(kSmCK + 8 * kAssignTS);           // u8[TS] coarse levels
-constexpr size_t kSmFK = align16(kSmCL + kAssignTS);               // u64[TS] fine keys
-constexpr size_t kSmFI = align16(kSmFK + 8 * kAssignTS);           // int[TS] entry of a position
+constexpr size_t kSmCK = align16(kSmBC + sizeof(BlockConst));      // u64[CS] coarse keys
+constexpr size_t kSmCL = align16(kSmCK + 8 * kAssignCS);           // u32[CS] coarse levels
+constexpr size_t kSmCB = align16(kSmCL + 4 * kAssignCS);           // u32[CS] coarse slot bases
+constexpr size_t kSmFK = align16(kSmCB + 4 * kAssignCS);           // u32[TS] cell slots
+constexpr size_t kSmFI = align16(kSmFK + 4 * kAssignTS);           // int[TS] entry of a position
 constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64[NL] key of an entry
-constexpr size_t kSmAcc = align16(kSmEK + 8 * kAssignNL);          // u32[14][NL] split sums
+constexpr size_t kSmES = align16(kSmEK + 8 * kAssignNL);           // u32[NL] slot of an entry
+constexpr size_t kSmAcc = align16(kSmES + 4 * kAssignNL);          // u32[14][NL] split sums
 constexpr size_t kSmCnt = align16(kSmAcc + 14 * 4 * kAssignNL);    // u32[NL] members
 constexpr size_t kSmCmax = align16(kSmCnt + 4 * kAssignNL);        // u32[NL] largest ordered C
 constexpr size_t kSmGmin = align16(kSmCmax + 4 * kAssignNL);       // u32[NL] lowest index at it
 constexpr size_t kSmMin = align16(kSmGmin + 4 * kAssignNL);        // int[NL] smallest exponent
 constexpr size_t kSmPid = align16(kSmMin + 4 * kAssignNL);         // u16[tile] gated pixels
-constexpr size_t kAssignSmem = align16(kSmPid + 2 * kTilePx);
+constexpr size_t kSmZ = align16(kSmPid + 2 * kTilePx);             // f32[tile] their depth
+constexpr size_t kSmC = align16(kSmZ + 4 * kTilePx);               // f32[tile] confidence
+constexpr size_t kSmRGB = align16(kSmC + 4 * kTilePx);             // u32[tile] colour
+constexpr size_t kAssignSmem = align16(kSmRGB + 4 * kTilePx);
 constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
 
 template <typename DT>
@@ -391,16 +458,21 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
   unsigned long long* s_ck = reinterpret_cast<unsigned long long*>(smem + kSmCK);
-  unsigned char* s_cl = smem + kSmCL;
-  unsigned long long* s_fk = reinterpret_cast<unsigned long long*>(smem + kSmFK);
+  unsigned* s_cl = reinterpret_cast<unsigned*>(smem + kSmCL);
+  unsigned* s_cb = reinterpret_cast<unsigned*>(smem + kSmCB);
+  unsigned* s_fk = reinterpret_cast<unsigned*>(smem + kSmFK);
   int* s_fi = reinterpret_cast<int*>(smem + kSmFI);
   unsigned long long* s_ek = reinterpret_cast<unsigned long long*>(smem + kSmEK);
+  unsigned* s_es = reinterpret_cast<unsigned*>(smem + kSmES);
   unsigned* s_acc = reinterpret_cast<unsigned*>(smem + kSmAcc);
   unsigned* s_cnt = reinterpret_cast<unsigned*>(smem + kSmCnt);
   unsigned* s_cmax = reinterpret_cast<unsigned*>(smem + kSmCmax);
   unsigned* s_gmin = reinterpret_cast<unsigned*>(smem + kSmGmin);
   int* s_min = reinterpret_cast<int*>(smem + kSmMin);
   unsigned short* s_pid = reinterpret_cast<unsigned short*>(smem + kSmPid);
+  float* s_z = reinterpret_cast<float*>(smem + kSmZ);
+  float* s_c = reinterpret_cast<float*>(smem + kSmC);
+  unsigned* s_rgb = reinterpret_cast<unsigned*>(smem + kSmRGB);
   __shared__ unsigned s_n, s_base, s_ng;
   __shared__ unsigned s_wc[2 * (kThreads / 32)];
 
@@ -420,8 +492,8 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     copy_words(&bc.nb[q], &rig.cam[src.j], sizeof(CamDev));
   }
   for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
-    s_ck[i] = kKeyEmpty;
-    s_fk[i] = kKeyEmpty;
+    if (i < kAssignCS) s_ck[i] = kKeyEmpty;
+    s_fk[i] = kSlotNone;
   }
   if (threadIdx.x == 0) s_n = 0;
 
@@ -434,6 +506,8 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   // (a) Eq. 9 gate, then compaction of the tile's gated pixels so that the per-point work
   // below runs on full warps
   unsigned gmask[2];
+  float zk[2] = {0.0f, 0.0f}, ck[2] = {0.0f, 0.0f};
+  unsigned rgbk[2] = {0u, 0u};
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int row = warp + 8 * k;
@@ -442,7 +516,13 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     if (x < W && y < H) {
       const long long li = (long long)y * W + x;
       const DT D = dep[li];
-      gated = Depth<DT>::valid(D) && (!rig.use_conf || cf[li] > rig.tau);
+      ck[k] = cf[li];
+      gated = Depth<DT>::valid(D) && (!rig.use_conf || ck[k] > rig.tau);
+      if (gated) {
+        zk[k] = Depth<DT>::z(D);
+        const uint8_t* px = col + 3 * li;
+        rgbk[k] = (unsigned)px[0] | ((unsigned)px[1] << 8) | ((unsigned)px[2] << 16);
+      }
       if (!gated && trace) {
         const long long g = rig.cam[cam].off + li;
         if (tr.pw) { tr.pw[3 * g] = qnan; tr.pw[3 * g + 1] = qnan; tr.pw[3 * g + 2] = qnan; }
@@ -471,8 +551,13 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int row = warp + 8 * k;
-    if ((gmask[k] >> lane) & 1u)
-      s_pid[s_wc[row] + __popc(gmask[k] & ((1u << lane) - 1u))] = (unsigned short)(row * kTileW + lane);
+    if ((gmask[k] >> lane) & 1u) {
+      const int pos = s_wc[row] + __popc(gmask[k] & ((1u << lane) - 1u));
+      s_pid[pos] = (unsigned short)(row * kTileW + lane);
+      s_z[pos] = zk[k];
+      s_c[pos] = ck[k];
+      s_rgb[pos] = rgbk[k];
+    }
   }
   __syncthreads();
   const int n_g = (int)s_ng;
@@ -485,17 +570,16 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   int mexp[2] = {0, 0};
   unsigned cord[2] = {0u, 0u};
   int hpos[2] = {0, 0};
-  long long gi[2] = {0, 0}, li[2] = {0, 0};
+  long long gi[2] = {0, 0};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int i = threadIdx.x + j * kThreads;
     if (i >= n_g) continue;
     const int pid = s_pid[i];
     const int x = tx * kTileW + (pid & (kTileW - 1)), y = ty * kTileH + pid / kTileW;
-    li[j] = (long long)y * W + x;
-    gi[j] = C.off + li[j];
-    const float z = Depth<DT>::z(dep[li[j]]);
-    const float c = cf[li[j]];
+    gi[j] = C.off + (long long)y * W + x;
+    const float z = s_z[i];
+    const float c = s_c[i];
     const float2 rx = __ldg(rays + C.ray_x + x), ry = __ldg(rays + C.ray_y + y);
     float P[3];
     world_point(C, z, rx.x, ry.x, P);                                 // Eq. 8
@@ -536,41 +620,55 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       if (tr.key && !has[j]) tr.key[gi[j]] = kKeyEmpty;
     }
     if (has[j]) {
-      hpos[j] = local_pos<kAssignTS>(s_ck, kKeyEmpty, coarse_key(r[j]));
+      hpos[j] = local_pos<kAssignCS>(s_ck, kKeyEmpty, coarse_key(r[j]));
       if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrCoarseFull); }
     }
   }
   __syncthreads();
-  // (c) Sec. II.5(1)d: level of each coarse cell present in the tile
-  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
+  // (c) Sec. II.5(1)d: level and slot range of each coarse cell present in the tile
+  for (int i = threadIdx.x; i < kAssignCS; i += kThreads) {
     const unsigned long long ck = s_ck[i];
-    if (ck != kKeyEmpty)
-      s_cl[i] = (unsigned char)level_for(coarse_count_of(t, ck), rig.n_min, rig.max_level);
+    if (ck == kKeyEmpty) continue;
+    const unsigned cs = coarse_find(t, ck);
+    s_cl[i] = cs != kSlotNone ? __ldcg(&t.clevel[cs]) : 0u;
+    s_cb[i] = cs != kSlotNone ? __ldcg(&t.cbase[cs]) : kSlotNone;
   }
   __syncthreads();
-  // (c) Sec. II.5(1)e: cell key and the point's offset inside its cell
+  // (c) Sec. II.5(1)e: cell key, its dense slot, and the point's offset inside the cell
   float frac[2][3];
+  unsigned long long fkey[2] = {kKeyEmpty, kKeyEmpty};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     if (!has[j]) continue;
-    const int l = s_cl[hpos[j]];
+    const int l = (int)s_cl[hpos[j]];
+    const unsigned base = s_cb[hpos[j]];
     const unsigned long long fk = fine_key(r[j], l);
     const int kk[3] = {(int)((fk >> 40) & 0xfffff) - kKeyBias, (int)((fk >> 20) & 0xfffff) - kKeyBias,
                        (int)(fk & 0xfffff) - kKeyBias};
+    const float sl = pow2f(l);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) frac[j][a] = __fsub_rn(ldexpf(r[j][a], l), (float)kk[a]);
-    hpos[j] = local_pos<kAssignTS>(s_fk, kKeyEmpty, fk);
-    if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrFineFull); }
+    for (int a = 0; a < 3; ++a) frac[j][a] = __fsub_rn(__fmul_rn(r[j][a], sl), (float)kk[a]);
+    // sub-cell of the coarse cell: k - (coarse << l) = k & (2^l - 1)
+    const unsigned mask = (1u << l) - 1u;
+    const unsigned local = ((((unsigned)kk[0] & mask) << l | ((unsigned)kk[1] & mask)) << l) |
+                           ((unsigned)kk[2] & mask);
+    if (base == kSlotNone) {                    // slot capacity exceeded (reported)
+      has[j] = false;
+    } else {
+      fkey[j] = fk;
+      hpos[j] = local_pos<kAssignTS>(s_fk, kSlotNone, base + local);
+      if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrSlots); }
+    }
     if (trace && tr.key) tr.key[gi[j]] = has[j] ? fk : kKeyEmpty;
   }
   __syncthreads();
   // compact the tile's cells: entry index per hash position
   for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
-    const unsigned long long fk = s_fk[i];
-    if (fk == kKeyEmpty) continue;
+    const unsigned slot = s_fk[i];
+    if (slot == kSlotNone) continue;
     const int e = (int)atomicAdd(&s_n, 1u);
     s_fi[i] = e;
-    s_ek[e] = fk;
+    s_es[e] = slot;
     s_cnt[e] = 0u;
     s_cmax[e] = 0u;
     s_gmin[e] = 0xffffffffu;
@@ -585,6 +683,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   for (int j = 0; j < 2; ++j) {
     if (!has[j]) continue;
     ent[j] = s_fi[hpos[j]];
+    s_ek[ent[j]] = fkey[j];                     // every member writes the same key
     atomicAdd(&s_cnt[ent[j]], 1u);
     atomicMax(&s_cmax[ent[j]], cord[j]);
     atomicMin(&s_min[ent[j]], mexp[j]);
@@ -598,14 +697,15 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     const int e = ent[j];
     if (cord[j] == s_cmax[e]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
     const int sh = mexp[j] - s_min[e];
-    const float w = sh > 62 ? 0.0f : ldexpf(mu[j], kFixShift - sh);
-    const uint8_t* px = col + 3 * li[j];
+    const float w = sh > 62 ? 0.0f : __fmul_rn(mu[j], pow2f(kFixShift - sh));
+    const unsigned rgb = s_rgb[threadIdx.x + j * kThreads];
     unsigned long long q[7];
     q[0] = __float2ull_rn(w);
 #pragma unroll
     for (int a = 0; a < 3; ++a) q[1 + a] = __float2ull_rn(__fmul_rn(w, frac[j][a]));
 #pragma unroll
-    for (int a = 0; a < 3; ++a) q[4 + a] = __float2ull_rn(__fmul_rn(w, (float)px[a] * 0.00390625f));
+    for (int a = 0; a < 3; ++a)
+      q[4 + a] = __float2ull_rn(__fmul_rn(w, (float)((rgb >> (8 * a)) & 0xffu) * 0.00390625f));
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
       atomicAdd(&s_acc[(2 * a) * kAssignNL + e], (unsigned)(q[a] & ((1ull << kLoBits) - 1ull)));
@@ -613,32 +713,49 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     }
   }
   __syncthreads();
-  // one partial record per (tile, cell), pushed onto the cell's list
+  // one partial record per (tile, cell); the link step files it under its cell
   const unsigned n_local = s_n;
   if (threadIdx.x == 0) s_base = atomicAdd(&t.cnt->n_partials, n_local);
   __syncthreads();
   for (int e = threadIdx.x; e < (int)n_local; e += kThreads) {
-    const unsigned slot = fine_insert(t, s_ek[e]);
     const unsigned pi = s_base + (unsigned)e;
-    if (slot == kSlotNone) continue;
     if (pi >= t.max_partials) { atomicOr(&t.cnt->error, kErrPartials); continue; }
     Partial p;
+    p.slot = s_es[e];
     p.count = s_cnt[e];
     p.mmin = s_min[e];
     p.pad = 0u;
+    t.fkey[p.slot] = s_ek[e];                   // the same value from every tile of the cell
     p.rep = ((unsigned long long)s_cmax[e] << 32) | (unsigned)(~s_gmin[e]);
 #pragma unroll
     for (int a = 0; a < 7; ++a)
       p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
                s_acc[(2 * a) * kAssignNL + e];
-    p.next = atomicExch(&t.fhead[slot], pi);
     t.part[pi] = p;
+  }
+}
+
+// ------------------------------------------------------------------ link step
+// Pushes every partial onto its cell's list and records the cell's smallest exponent; the
+// first partial of a cell also claims the cell for the reduce step.
+__global__ void __launch_bounds__(kThreads) k_link(Tables t) {
+  const unsigned np = min(t.cnt->n_partials, t.max_partials);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    const unsigned slot = t.part[i].slot;
+    const int mm = t.part[i].mmin;
+    atomicMin(&t.fmmin[slot], mm);
+    const unsigned prev = atomicExch(&t.fhead[slot], i);
+    t.pnext[i] = prev;
+    if (prev == kSlotNone) {
+      const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
+      if (n < t.max_slots) t.fused[n] = slot;
+    }
   }
 }
 
 // ------------------------------------------------------------------ reduce step
 __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
-  const unsigned n_cells = min(t.cnt->n_cells, t.fmask + 1u);
+  const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
   const unsigned n_part = min(t.cnt->n_partials, t.max_partials);
   const unsigned n = max(n_cells, n_coarse);
@@ -647,22 +764,18 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
       const unsigned slot = t.fused[i];
       const unsigned long long key = t.fkey[slot];
       const unsigned head = t.fhead[slot];
+      const int mmin = t.fmmin[slot];
       unsigned count = 0u, steps = 0u;
       unsigned long long rep = 0ull;
-      int mmin = INT_MAX;
-      for (unsigned p = head; p != kSlotNone && steps <= n_part; p = t.part[p].next, ++steps) {
-        const Partial& P = t.part[p];
+      unsigned long long S[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+      for (unsigned p = head; p != kSlotNone && steps <= n_part; ++steps) {
+        const Partial P = t.part[p];
         count += P.count;
         rep = max(rep, P.rep);
-        mmin = min(mmin, P.mmin);
-      }
-      unsigned long long S[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-      steps = 0u;
-      for (unsigned p = head; p != kSlotNone && steps <= n_part; p = t.part[p].next, ++steps) {
-        const Partial& P = t.part[p];
-        const int sh = P.mmin - mmin;
+        const int sh = P.mmin - mmin;          // shift to the cell's smallest exponent
 #pragma unroll
         for (int a = 0; a < 7; ++a) S[a] += sh < 64 ? (P.s[a] >> sh) : 0ull;
+        p = t.pnext[p];
       }
       if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
       const unsigned g = head != kSlotNone ? ~(unsigned)(rep & 0xffffffffull) : 0xffffffffu;
@@ -685,10 +798,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
       c.rep = g;
       c.pad = 0u;
       c.key = key;
-      t.staged[i] = c;
-      if (head != kSlotNone) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));
-      t.fkey[slot] = kKeyEmpty;                 // ready for the next frame
-      t.fhead[slot] = kSlotNone;
+      if ((long long)i < out.max_cells) {
+        t.staged[i] = c;
+        if (head != kSlotNone) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));
+      }
+      t.fhead[slot] = kSlotNone;                // ready for the next frame
+      t.fmmin[slot] = INT_MAX;
     }
     if (i < n_coarse) {
       const unsigned cs = t.cused[i];
@@ -725,39 +840,33 @@ __device__ __forceinline__ unsigned block_excl_scan_1024(unsigned v, unsigned* s
   return before + x - v;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_words(Tables t) {
+// Block b scans bitmap words [1024 b, 1024 b + 1024) and folds a share of the count step's
+// per-block statistics into the frame counters; the last block to finish (a fenced
+// counter, no waiting) scans the per-block sums and writes the frame statistics.
+__global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
   __shared__ unsigned s_w[32];
+  __shared__ unsigned long long s_l[3][32];
+  __shared__ unsigned s_b[6][32];
+  __shared__ bool s_last;
   const long long w = (long long)blockIdx.x * 1024 + threadIdx.x;
   const unsigned v = (w < t.n_words) ? __popc(t.bitmap[w]) : 0u;
   unsigned total;
   const unsigned ex = block_excl_scan_1024(v, s_w, total);
   if (w < t.n_words) t.wprefix[w] = ex;
   if (threadIdx.x == 0) t.bsum[blockIdx.x] = total;
-}
 
-__global__ void __launch_bounds__(1024) k_scan_blocks(Tables t, OutDev out) {
-  __shared__ unsigned s_w[32];
-  unsigned carry = 0;
-  for (int base = 0; base < t.n_wblocks; base += 1024) {
-    const int i = base + threadIdx.x;
-    const unsigned v = (i < t.n_wblocks) ? t.bsum[i] : 0u;
-    unsigned total;
-    const unsigned ex = block_excl_scan_1024(v, s_w, total);
-    if (i < t.n_wblocks) t.bsum[i] = carry + ex;
-    carry += total;
-  }
-  // frame statistics from the per-block partials of the count step
+  // statistics of the count step's blocks [b0, b1)
+  const int per = (t.n_bstats + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * per, b1 = min(t.n_bstats, b0 + per);
   unsigned long long nv = 0, ng = 0, noor = 0;
   unsigned bmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, bmax[3] = {0u, 0u, 0u};
-  for (int i = threadIdx.x; i < t.n_bstats; i += 1024) {
+  for (int i = b0 + threadIdx.x; i < b1; i += 1024) {
     const BlockStats b = t.bstats[i];
     nv += b.n_valid;
     ng += b.n_gated;
     noor += b.n_oor;
     for (int k = 0; k < 3; ++k) { bmin[k] = min(bmin[k], b.bmin[k]); bmax[k] = max(bmax[k], b.bmax[k]); }
   }
-  __shared__ unsigned long long s_l[3][32];
-  __shared__ unsigned s_b[6][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) {
     nv += __shfl_xor_sync(0xffffffffu, nv, o);
@@ -774,32 +883,60 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Tables t, OutDev out) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    fuseflow_stats st = {};
+    unsigned long long a0 = 0, a1 = 0, a2 = 0;
     unsigned mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
-    for (int w = 0; w < 32; ++w) {
-      st.n_valid += (int64_t)s_l[0][w];
-      st.n_gated += (int64_t)s_l[1][w];
-      st.n_out_of_range += (int64_t)s_l[2][w];
-      for (int k = 0; k < 3; ++k) { mn[k] = min(mn[k], s_b[k][w]); mx[k] = max(mx[k], s_b[3 + k][w]); }
+    for (int q = 0; q < 32; ++q) {
+      a0 += s_l[0][q]; a1 += s_l[1][q]; a2 += s_l[2][q];
+      for (int k = 0; k < 3; ++k) { mn[k] = min(mn[k], s_b[k][q]); mx[k] = max(mx[k], s_b[3 + k][q]); }
     }
-    const unsigned nc = t.cnt->n_cells;
-    unsigned err = t.cnt->error;
+    if (a0) atomicAdd(&t.cnt->n_valid, a0);
+    if (a1) atomicAdd(&t.cnt->n_gated, a1);
+    if (a2) atomicAdd(&t.cnt->n_oor, a2);
+    for (int k = 0; k < 3; ++k) {
+      if (mn[k] != 0xffffffffu) atomicMax(&t.cnt->bmin_inv[k], ~mn[k]);
+      if (mx[k] != 0u) atomicMax(&t.cnt->bmax[k], mx[k]);
+    }
+    __threadfence();
+    s_last = atomicAdd(&t.cnt->scan_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: exclusive scan of the per-block sums, then the frame statistics
+  unsigned carry = 0;
+  for (int base = 0; base < t.n_wblocks; base += 1024) {
+    const int i = base + threadIdx.x;
+    const unsigned bv = (i < t.n_wblocks) ? __ldcg(&t.bsum[i]) : 0u;
+    unsigned tot;
+    const unsigned bex = block_excl_scan_1024(bv, s_w, tot);
+    if (i < t.n_wblocks) t.bsum[i] = carry + bex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    const FrameCounters& c = *t.cnt;
+    fuseflow_stats st = {};
+    st.n_valid = (int64_t)__ldcg(&c.n_valid);
+    st.n_gated = (int64_t)__ldcg(&c.n_gated);
+    st.n_out_of_range = (int64_t)__ldcg(&c.n_oor);
+    const unsigned nc = __ldcg(&c.n_cells);
+    unsigned err = __ldcg(&c.error);
     if ((long long)nc > out.max_cells) err |= kErrCells;
-    if (t.cnt->n_partials > t.max_partials) err |= kErrPartials;
+    if (__ldcg(&c.n_partials) > t.max_partials) err |= kErrPartials;
     st.n_cells = (int64_t)(nc < out.max_cells ? nc : out.max_cells);
     for (int k = 0; k < 3; ++k) {
-      st.bbox[k] = st.n_gated ? (float)((double)from_ordered(mn[k]) * out.unit_m) : __int_as_float(0x7f800000);
-      st.bbox[3 + k] = st.n_gated ? (float)((double)from_ordered(mx[k]) * out.unit_m) : __int_as_float(0xff800000);
+      const unsigned mn = ~__ldcg(&c.bmin_inv[k]), mx = __ldcg(&c.bmax[k]);
+      st.bbox[k] = st.n_gated ? (float)((double)from_ordered(mn) * out.unit_m) : __int_as_float(0x7f800000);
+      st.bbox[3 + k] = st.n_gated ? (float)((double)from_ordered(mx) * out.unit_m) : __int_as_float(0xff800000);
     }
     st.error = (int32_t)err;
-    st.n_coarse = (int32_t)t.cnt->n_coarse;
+    st.n_coarse = (int32_t)__ldcg(&c.n_coarse);
     *out.stats = st;
   }
 }
 
 // ------------------------------------------------------------------ emit
 __global__ void __launch_bounds__(kThreads) k_emit(Tables t, OutDev out) {
-  const unsigned n_cells = min(t.cnt->n_cells, t.fmask + 1u);
+  const unsigned n_cells = (unsigned)min((long long)min(t.cnt->n_cells, t.max_slots), out.max_cells);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
     const CellOut c = t.staged[i];
     const unsigned g = c.rep;
@@ -828,6 +965,7 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
     if (i < fcap) {
       t.fkey[i] = kKeyEmpty;
       t.fhead[i] = kSlotNone;
+      t.fmmin[i] = INT_MAX;
     }
     if (i < ccap) {
       t.ckey[i] = kKeyEmpty;
@@ -852,18 +990,20 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   cudaError_t err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
   if (err != cudaSuccess) return err;
   mark(1);
-  k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x);
+  k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x,
+                                                                       geo.count_chunks);
   mark(2);
   k_assign<DT><<<dim3(geo.tiles_max, geo.n_cams), kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr,
                                                                                 (float)out.unit_m);
   mark(3);
-  k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  k_link<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(4);
-  k_scan_words<<<t.n_wblocks, 1024, 0, s>>>(t);
-  k_scan_blocks<<<1, 1024, 0, s>>>(t, out);
+  k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
   mark(5);
-  k_emit<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  k_scan<<<t.n_wblocks, 1024, 0, s>>>(t, out);
   mark(6);
+  k_emit<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  mark(7);
   return cudaGetLastError();
 }
 
