@@ -30,6 +30,7 @@ struct fuseflow_ctx {
   unsigned max_slots = 0, ccap = 0;
   RigDev* d_rig = nullptr;
   float2* d_rays = nullptr;
+  void* d_blocks = nullptr;            // tile list + per-camera block constants
   Tables tab{};
   void* d_tables = nullptr;            // one allocation for every table
   size_t table_bytes = 0;
@@ -182,6 +183,7 @@ void fuseflow_destroy(fuseflow_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaFree(ctx->d_rig);
   cudaFree(ctx->d_rays);
+  cudaFree(ctx->d_blocks);
   cudaFree(ctx->d_tables);
   cudaFree(ctx->d_out);
   cudaFree(ctx->d_stage);
@@ -321,10 +323,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const size_t o_fhead = take(sizeof(unsigned) * ctx->max_slots, 256);
   const size_t o_fmmin = take(sizeof(int) * ctx->max_slots, 256);
   const size_t o_fused = take(sizeof(unsigned) * ctx->max_slots, 256);
-  const size_t o_ckey = take(sizeof(unsigned long long) * ctx->ccap, 256);
-  const size_t o_ccnt = take(sizeof(unsigned) * ctx->ccap, 256);
-  const size_t o_clev = take(sizeof(unsigned) * ctx->ccap, 256);
-  const size_t o_cbase = take(sizeof(unsigned) * ctx->ccap, 256);
+  const size_t o_coarse = take(sizeof(CoarseEntry) * ctx->ccap, 256);
   const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
@@ -345,8 +344,16 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const size_t q_key = take_out(sizeof(unsigned long long) * (size_t)ctx->max_cells);
   ctx->out_bytes = po;
 
+  const int n_tiles = n_tiles_for(*rig);
+  std::vector<TileDesc> tiles((size_t)n_tiles);
+  std::vector<BlockConst> bconst((size_t)n_cams);
+  fill_tiles(*rig, tiles.data());
+  fill_block_consts(*rig, bconst.data());
+  const size_t tiles_bytes = align_up(sizeof(TileDesc) * (size_t)n_tiles, 256);
+  const size_t blocks_bytes = tiles_bytes + sizeof(BlockConst) * (size_t)n_cams;
   if (cudaMalloc(&ctx->d_rig, sizeof(RigDev)) != cudaSuccess ||
       cudaMalloc(&ctx->d_rays, sizeof(float2) * rays.size()) != cudaSuccess ||
+      cudaMalloc(&ctx->d_blocks, blocks_bytes) != cudaSuccess ||
       cudaMalloc(&ctx->d_tables, ctx->table_bytes) != cudaSuccess ||
       cudaMalloc(&ctx->d_out, ctx->out_bytes) != cudaSuccess) {
     status = FUSEFLOW_ERR_OUT_OF_MEMORY;
@@ -359,12 +366,12 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     t.fmmin = reinterpret_cast<int*>(b + o_fmmin);
     t.fused = reinterpret_cast<unsigned*>(b + o_fused);
     t.max_slots = ctx->max_slots;
-    t.ckey = reinterpret_cast<unsigned long long*>(b + o_ckey);
-    t.ccount = reinterpret_cast<unsigned*>(b + o_ccnt);
-    t.clevel = reinterpret_cast<unsigned*>(b + o_clev);
-    t.cbase = reinterpret_cast<unsigned*>(b + o_cbase);
+    t.coarse = reinterpret_cast<CoarseEntry*>(b + o_coarse);
     t.n_min = params->n_min;
     t.max_level = params->max_level;
+    t.tiles = static_cast<const TileDesc*>(ctx->d_blocks);
+    t.bconst = reinterpret_cast<const BlockConst*>(static_cast<char*>(ctx->d_blocks) + tiles_bytes);
+    t.n_tiles = n_tiles;
     t.cused = reinterpret_cast<unsigned*>(b + o_cused);
     t.cmask = ctx->ccap - 1;
     t.cnt = reinterpret_cast<FrameCounters*>(b + o_cnt);
@@ -393,6 +400,9 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     od.unit_m = unit;
     if (cudaMemcpy(ctx->d_rig, rig, sizeof(RigDev), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_rays, rays.data(), sizeof(float2) * rays.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_blocks, tiles.data(), sizeof(TileDesc) * (size_t)n_tiles, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(static_cast<char*>(ctx->d_blocks) + tiles_bytes, bconst.data(),
+                   sizeof(BlockConst) * (size_t)n_cams, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->d_tables, 0, ctx->table_bytes) != cudaSuccess ||
         cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
         launch_init_tables(t, ctx->max_slots, ctx->ccap, 0) != cudaSuccess ||
@@ -604,6 +614,7 @@ constexpr long long kStaticMaxCells = 1ll << 15;       // 32,768 output cells
 constexpr unsigned kStaticSlots = 1u << 18;            // dense cell slots
 constexpr unsigned kStaticCoarse = 1u << 16;           // coarse hash slots
 constexpr int kStaticMaxRays = 1 << 16;                // sum over cameras of W + H
+constexpr int kStaticMaxTiles = (int)(kStaticMaxPixels / 512) + 4 * kMaxCams;   // 32x16 tiles
 constexpr long long kStaticWords = kStaticMaxPixels / 32;
 constexpr int kStaticWBlocks = (int)((kStaticWords + 1023) / 1024);
 constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 1024 + 1);   // chunks = 1
@@ -612,15 +623,14 @@ constexpr int kStaticMaxDevices = 64;
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kSRig = 0;
 constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
-constexpr size_t kSFKey = al256(kSRays + sizeof(float2) * kStaticMaxRays);
+constexpr size_t kSTiles = al256(kSRays + sizeof(float2) * kStaticMaxRays);
+constexpr size_t kSBConst = al256(kSTiles + sizeof(TileDesc) * kStaticMaxTiles);
+constexpr size_t kSFKey = al256(kSBConst + sizeof(BlockConst) * kMaxCams);
 constexpr size_t kSFHead = al256(kSFKey + sizeof(unsigned long long) * kStaticSlots);
 constexpr size_t kSFMmin = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSFused = al256(kSFMmin + sizeof(int) * kStaticSlots);
-constexpr size_t kSCKey = al256(kSFused + sizeof(unsigned) * kStaticSlots);
-constexpr size_t kSCCount = al256(kSCKey + sizeof(unsigned long long) * kStaticCoarse);
-constexpr size_t kSCLev = al256(kSCCount + sizeof(unsigned) * kStaticCoarse);
-constexpr size_t kSCBase = al256(kSCLev + sizeof(unsigned) * kStaticCoarse);
-constexpr size_t kSCUsed = al256(kSCBase + sizeof(unsigned) * kStaticCoarse);
+constexpr size_t kSCoarse = al256(kSFused + sizeof(unsigned) * kStaticSlots);
+constexpr size_t kSCUsed = al256(kSCoarse + sizeof(CoarseEntry) * kStaticCoarse);
 constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticCoarse);
 constexpr size_t kSBStats = al256(kSCnt + sizeof(FrameCounters) + sizeof(unsigned) * kStaticWords);
 constexpr size_t kSPart = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
@@ -637,6 +647,8 @@ std::mutex g_static_mutex;                             // guards the host stagin
 unsigned char* g_static_dev[kStaticMaxDevices] = {};   // device address per device
 RigDev g_static_rig;                                   // host staging of the rig constants
 float2 g_static_rays[kStaticMaxRays];                  // host staging of the ray tables
+TileDesc g_static_tiles[kStaticMaxTiles];              // host staging of the tile list
+BlockConst g_static_bconst[kMaxCams];                  // host staging of the block constants
 
 // The neighbour rule of neighbour_table() above (Sec. II.5(2)b: optical-axis angle, then
 // centre distance, then index, 1e-9 tolerance) on fixed-size arrays: no heap use.
@@ -680,10 +692,7 @@ Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   t.fmmin = reinterpret_cast<int*>(base + kSFMmin);
   t.fused = reinterpret_cast<unsigned*>(base + kSFused);
   t.max_slots = kStaticSlots;
-  t.ckey = reinterpret_cast<unsigned long long*>(base + kSCKey);
-  t.ccount = reinterpret_cast<unsigned*>(base + kSCCount);
-  t.clevel = reinterpret_cast<unsigned*>(base + kSCLev);
-  t.cbase = reinterpret_cast<unsigned*>(base + kSCBase);
+  t.coarse = reinterpret_cast<CoarseEntry*>(base + kSCoarse);
   t.cused = reinterpret_cast<unsigned*>(base + kSCUsed);
   t.cmask = kStaticCoarse - 1;
   t.cnt = reinterpret_cast<FrameCounters*>(base + kSCnt);
@@ -743,7 +752,11 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
     if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
   }
   const long long max_cells = params->max_cells > 0 ? params->max_cells : kStaticMaxCells;
-  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells)
+  int n_tiles_req = 0;
+  for (int i = 0; i < n_cams; ++i)
+    n_tiles_req += ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16);
+  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells ||
+      n_tiles_req > kStaticMaxTiles)
     return FUSEFLOW_ERR_CAPACITY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
@@ -819,8 +832,15 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
       for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
     }
   }
+  const int n_tiles = n_tiles_for(rig);
+  fill_tiles(rig, g_static_tiles);
+  fill_block_consts(rig, g_static_bconst);
   // pageable host -> device copies return once the host buffers have been read
-  if (cudaMemcpyAsync(base + kSRig, &rig, sizeof(RigDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(base + kSTiles, g_static_tiles, sizeof(TileDesc) * (size_t)n_tiles,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + kSBConst, g_static_bconst, sizeof(BlockConst) * (size_t)n_cams,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + kSRig, &rig, sizeof(RigDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + kSRays, g_static_rays, sizeof(float2) * (size_t)nr, cudaMemcpyHostToDevice,
                       s) != cudaSuccess)
     return FUSEFLOW_ERR_CUDA;
@@ -837,6 +857,9 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
   t.n_min = params->n_min;
   t.max_level = params->max_level;
+  t.tiles = reinterpret_cast<const TileDesc*>(base + kSTiles);
+  t.bconst = reinterpret_cast<const BlockConst*>(base + kSBConst);
+  t.n_tiles = n_tiles;
   OutDev od{};
   od.stats = stats;
   od.pos = pos;

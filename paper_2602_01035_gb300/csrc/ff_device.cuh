@@ -67,6 +67,21 @@ struct RigDev {
   PairDev pair[kMaxCams * kMaxK1];
 };
 
+// Constants of one camera's tiles: the camera, its K-1 neighbour pairs and the neighbour
+// cameras, contiguous so that a block copies them to shared memory in one round trip.
+struct BlockConst {
+  CamDev cam;
+  PairDev pair[kMaxK1];
+  CamDev nb[kMaxK1];
+};
+
+// One 32x16 tile of one camera (the assign step's unit of work).
+struct __align__(32) TileDesc {
+  int cam, x0, y0, W;
+  int H, k1;
+  long long off;                 // global index of the camera's pixel (0, 0)
+};
+
 // Per (tile, cell) partial result of the assign step; the link step pushes it onto its
 // cell's list (next[] holds the links).  Sums are exact integers in units of
 // 2^-(kFixShift + mmin) of the tile's own smallest weight exponent mmin; the reduce step
@@ -80,6 +95,15 @@ struct __align__(16) Partial {
   unsigned long long s[7];       // sums of w, w frac_x, w frac_y, w frac_z, w r, w g, w b
 };
 static_assert(sizeof(Partial) == 80, "partial record layout");
+
+// Coarse hash-table record: key, density count (Sec. II.5(1)c) and, once every count is
+// in, the level and first dense cell slot packed as level << 27 | base.
+struct __align__(16) CoarseEntry {
+  unsigned long long key;
+  unsigned count;
+  unsigned lvbase;
+};
+constexpr unsigned kBaseNone = (1u << 27) - 1u;    // base field of a coarse cell without slots
 
 // Fused cell staged by the reduce step (indexed by insertion order) for the emit step.
 struct __align__(16) CellOut {

@@ -23,10 +23,7 @@ struct Tables {                  // context-owned device scratch
   unsigned* fused;               // used slots, in claim order
   unsigned max_slots;
   // coarse hash table (open addressing), ccap entries
-  unsigned long long* ckey;
-  unsigned* ccount;
-  unsigned* clevel;              // refinement level of the coarse cell
-  unsigned* cbase;               // first dense slot of the coarse cell
+  CoarseEntry* coarse;
   unsigned* cused;
   unsigned cmask;
   FrameCounters* cnt;
@@ -42,6 +39,9 @@ struct Tables {                  // context-owned device scratch
   long long n_words;
   int n_wblocks;
   int n_min, max_level;          // level rule (Sec. II.5(1)d)
+  const TileDesc* tiles;         // assign-step tiles, n_tiles entries
+  const BlockConst* bconst;      // per-camera block constants
+  int n_tiles;
 };
 
 struct TraceDev {
@@ -75,6 +75,12 @@ struct Geometry {
 };
 
 cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cudaStream_t s);
+
+// Host-side construction of the assign step's tile list and per-camera block constants
+// from the rig constants (caller-sized arrays: n_tiles_for(rig) and rig.n_cams entries).
+int n_tiles_for(const RigDev& rig);
+void fill_tiles(const RigDev& rig, TileDesc* out);
+void fill_block_consts(const RigDev& rig, BlockConst* out);
 // ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp,
                          const Tables& t, const TraceDev& tr, const OutDev& out,

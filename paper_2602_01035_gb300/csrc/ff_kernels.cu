@@ -42,10 +42,10 @@ constexpr float kInvLn2 = 1.44269504088896340736f;
 __device__ __forceinline__ unsigned coarse_insert(const Tables& t, unsigned long long key) {
   unsigned h = (unsigned)mix64(key) & t.cmask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    unsigned long long cur = __ldcg(&t.ckey[h]);
+    unsigned long long cur = __ldcg(&t.coarse[h].key);
     if (cur == key) return h;
     if (cur == kKeyEmpty) {
-      cur = atomicCAS(&t.ckey[h], kKeyEmpty, key);
+      cur = atomicCAS(&t.coarse[h].key, kKeyEmpty, key);
       if (cur == kKeyEmpty) {
         const unsigned n = atomicAdd(&t.cnt->n_coarse, 1u);
         if (n <= t.cmask) t.cused[n] = h;
@@ -59,17 +59,18 @@ __device__ __forceinline__ unsigned coarse_insert(const Tables& t, unsigned long
   return kSlotNone;
 }
 
-// Coarse hash slot of an existing coarse key (inserted by the count step).
-__device__ __forceinline__ unsigned coarse_find(const Tables& t, unsigned long long key) {
-  unsigned h = (unsigned)mix64(key) & t.cmask;
+// Level and slot base (packed level << 27 | base) of an existing coarse key, continuing a
+// probe whose first record `e` (at position h) was loaded earlier.
+__device__ __forceinline__ unsigned coarse_lvbase(const Tables& t, unsigned long long key,
+                                                  unsigned h, ulonglong2 e) {
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    const unsigned long long cur = __ldcg(&t.ckey[h]);
-    if (cur == key) return h;
-    if (cur == kKeyEmpty) break;
+    if (e.x == key) return (unsigned)(e.y >> 32);
+    if (e.x == kKeyEmpty) break;
     h = (h + 1) & t.cmask;
+    e = __ldcg(reinterpret_cast<const ulonglong2*>(&t.coarse[h]));
   }
   atomicOr(&t.cnt->error, kErrCoarseMiss);
-  return kSlotNone;
+  return kBaseNone;
 }
 
 template <int NT, typename T>
@@ -111,15 +112,14 @@ __device__ void assign_levels(Tables& t) {
     unsigned long long size = 0;
     if (i < n_coarse) {
       cs = __ldcg(&t.cused[i]);
-      l = (unsigned)level_for(__ldcg(&t.ccount[cs]), t.n_min, t.max_level);
+      l = (unsigned)level_for(__ldcg(&t.coarse[cs].count), t.n_min, t.max_level);
       size = 1ull << (3 * l);                  // 8^l <= 2^42
     }
     unsigned long long total;
     const unsigned long long ex = block_excl_scan<kThreads, unsigned long long>(size, s_w, total);
     if (i < n_coarse) {
       const unsigned long long b = carry + ex;
-      t.clevel[cs] = l;
-      t.cbase[cs] = b + size <= t.max_slots ? (unsigned)b : kSlotNone;
+      t.coarse[cs].lvbase = (l << 27) | (b + size <= t.max_slots ? (unsigned)b : kBaseNone);
     }
     carry += total;
   }
@@ -148,12 +148,6 @@ __device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe =
 // ------------------------------------------------------------------ block constants
 // The tile's camera, its K-1 neighbour pairs and the neighbour cameras, staged in shared
 // memory once per block (every pixel of a tile belongs to the same camera).
-struct BlockConst {
-  CamDev cam;
-  PairDev pair[kMaxK1];
-  CamDev nb[kMaxK1];
-};
-
 __device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes) {
   int* d = static_cast<int*>(dst);
   const int* s = static_cast<const int*>(src);
@@ -375,7 +369,7 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
         atomicAdd(&s_cnt[h], rn[j]);
       } else {
         const unsigned slot = coarse_insert(t, rk[j]);
-        if (slot != kSlotNone) atomicAdd(&t.ccount[slot], rn[j]);
+        if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, rn[j]);
       }
     }
   }
@@ -412,7 +406,7 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     const unsigned long long key = s_key[i];
     if (key == kKeyEmpty) continue;
     const unsigned slot = coarse_insert(t, key);
-    if (slot != kSlotNone) atomicAdd(&t.ccount[slot], s_cnt[i]);
+    if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, s_cnt[i]);
   }
   // the last block to finish (fenced counter, no waiting) sizes the cells' slot ranges
   __threadfence();
@@ -428,14 +422,10 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
 
 // ------------------------------------------------------------------ assign step
 constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
-constexpr int kAssignCS = kTilePx;         // coarse-key positions (coarse keys <= pixels)
 constexpr int kAssignNL = kTilePx;         // distinct fine cells of a tile, at most
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 constexpr size_t kSmBC = 0;
-constexpr size_t kSmCK = align16(kSmBC + sizeof(BlockConst));      // u64[CS] coarse keys
-constexpr size_t kSmCL = align16(kSmCK + 8 * kAssignCS);           // u32[CS] coarse levels
-constexpr size_t kSmCB = align16(kSmCL + 4 * kAssignCS);           // u32[CS] coarse slot bases
-constexpr size_t kSmFK = align16(kSmCB + 4 * kAssignCS);           // u32[TS] cell slots
+constexpr size_t kSmFK = align16(kSmBC + sizeof(BlockConst));      // u32[TS] cell slots
 constexpr size_t kSmFI = align16(kSmFK + 4 * kAssignTS);           // int[TS] entry of a position
 constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64[NL] key of an entry
 constexpr size_t kSmES = align16(kSmEK + 8 * kAssignNL);           // u32[NL] slot of an entry
@@ -451,15 +441,19 @@ constexpr size_t kSmRGB = align16(kSmC + 4 * kTilePx);             // u32[tile] 
 constexpr size_t kAssignSmem = align16(kSmRGB + 4 * kTilePx);
 constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
 
+// First probe of a point's coarse record (read-only during the assign step, L1-cached);
+// coarse_lvbase() finishes the probe once the value is needed.
+__device__ __forceinline__ ulonglong2 coarse_probe(const Tables& t, unsigned long long key, unsigned& h) {
+  h = (unsigned)mix64(key) & t.cmask;
+  return __ldg(reinterpret_cast<const ulonglong2*>(&t.coarse[h]));
+}
+
 template <typename DT>
 __global__ void __launch_bounds__(kThreads, 3)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m) {
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
-  unsigned long long* s_ck = reinterpret_cast<unsigned long long*>(smem + kSmCK);
-  unsigned* s_cl = reinterpret_cast<unsigned*>(smem + kSmCL);
-  unsigned* s_cb = reinterpret_cast<unsigned*>(smem + kSmCB);
   unsigned* s_fk = reinterpret_cast<unsigned*>(smem + kSmFK);
   int* s_fi = reinterpret_cast<int*>(smem + kSmFI);
   unsigned long long* s_ek = reinterpret_cast<unsigned long long*>(smem + kSmEK);
@@ -474,57 +468,54 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   float* s_c = reinterpret_cast<float*>(smem + kSmC);
   unsigned* s_rgb = reinterpret_cast<unsigned*>(smem + kSmRGB);
   __shared__ unsigned s_n, s_base, s_ng;
-  __shared__ unsigned s_wc[2 * (kThreads / 32)];
 
   const RigDev& rig = *rigp;
-  const int cam = blockIdx.y;
-  const int W = rig.cam[cam].W, H = rig.cam[cam].H;
-  const int tiles_x = (W + kTileW - 1) / kTileW;
-  const int tiles_y = (H + kTileH - 1) / kTileH;
-  if ((int)blockIdx.x >= tiles_x * tiles_y) return;
-  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const TileDesc td = t.tiles[blockIdx.x];
+  const int cam = td.cam, W = td.W, H = td.H, k1 = td.k1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k1 = rig.k1;
-  copy_words(&bc.cam, &rig.cam[cam], sizeof(CamDev));
-  for (int q = 0; q < k1; ++q) {
-    const PairDev& src = rig.pair[rig.cam[cam].pair0 + q];
-    copy_words(&bc.pair[q], &src, sizeof(PairDev));
-    copy_words(&bc.nb[q], &rig.cam[src.j], sizeof(CamDev));
-  }
-  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
-    if (i < kAssignCS) s_ck[i] = kKeyEmpty;
-    s_fk[i] = kSlotNone;
-  }
-  if (threadIdx.x == 0) s_n = 0;
-
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
   const uint8_t* __restrict__ col = fp.rgb[cam];
+  // issue the tile's image loads and the constant copy together (one round trip)
+  DT Dk[2];
+  float ckv[2];
+  unsigned rgbk[2] = {0u, 0u};
+  bool inimg[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = td.x0 + lane, y = td.y0 + warp + 8 * k;
+    inimg[k] = x < W && y < H;
+    Dk[k] = (DT)0;
+    ckv[k] = 0.0f;
+    if (inimg[k]) {
+      const long long li = (long long)y * W + x;
+      Dk[k] = dep[li];
+      ckv[k] = cf[li];
+      const uint8_t* px = col + 3 * li;
+      rgbk[k] = (unsigned)px[0] | ((unsigned)px[1] << 8) | ((unsigned)px[2] << 16);
+    }
+  }
+  const BlockConst& gbc = t.bconst[cam];
+  copy_words(&bc.cam, &gbc.cam, sizeof(CamDev));
+  copy_words(bc.pair, gbc.pair, k1 * (int)sizeof(PairDev));
+  copy_words(bc.nb, gbc.nb, k1 * (int)sizeof(CamDev));
+  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) s_fk[i] = kSlotNone;
+  if (threadIdx.x == 0) { s_n = 0; s_ng = 0; }
+  __syncthreads();
+
   const bool trace = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
   const float qnan = __int_as_float(0x7fc00000);
 
-  // (a) Eq. 9 gate, then compaction of the tile's gated pixels so that the per-point work
-  // below runs on full warps
-  unsigned gmask[2];
-  float zk[2] = {0.0f, 0.0f}, ck[2] = {0.0f, 0.0f};
-  unsigned rgbk[2] = {0u, 0u};
+  // (a) Eq. 9 gate and compaction of the tile's gated pixels (any order: every reduction
+  // below is order-independent), so that the per-point work runs on full warps
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int row = warp + 8 * k;
-    const int x = tx * kTileW + lane, y = ty * kTileH + row;
     bool gated = false;
-    if (x < W && y < H) {
-      const long long li = (long long)y * W + x;
-      const DT D = dep[li];
-      ck[k] = cf[li];
-      gated = Depth<DT>::valid(D) && (!rig.use_conf || ck[k] > rig.tau);
-      if (gated) {
-        zk[k] = Depth<DT>::z(D);
-        const uint8_t* px = col + 3 * li;
-        rgbk[k] = (unsigned)px[0] | ((unsigned)px[1] << 8) | ((unsigned)px[2] << 16);
-      }
+    if (inimg[k]) {
+      gated = Depth<DT>::valid(Dk[k]) && (!rig.use_conf || ckv[k] > rig.tau);
       if (!gated && trace) {
-        const long long g = rig.cam[cam].off + li;
+        const long long g = td.off + (long long)(td.y0 + row) * W + td.x0 + lane;
         if (tr.pw) { tr.pw[3 * g] = qnan; tr.pw[3 * g + 1] = qnan; tr.pw[3 * g + 2] = qnan; }
         if (tr.e) tr.e[g] = qnan;
         if (tr.omega) tr.omega[g] = qnan;
@@ -532,30 +523,15 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
         if (tr.key) tr.key[g] = kKeyEmpty;
       }
     }
-    gmask[k] = __ballot_sync(0xffffffffu, gated);
-    if (lane == 0) s_wc[row] = __popc(gmask[k]);
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {            // exclusive scan of the 16 row counts
-    const unsigned v = threadIdx.x < 16 ? s_wc[threadIdx.x] : 0u;
-    unsigned x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (threadIdx.x < 16) s_wc[threadIdx.x] = x - v;
-    if (threadIdx.x == 15) s_ng = x;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int row = warp + 8 * k;
-    if ((gmask[k] >> lane) & 1u) {
-      const int pos = s_wc[row] + __popc(gmask[k] & ((1u << lane) - 1u));
+    const unsigned gmask = __ballot_sync(0xffffffffu, gated);
+    unsigned wbase = 0u;
+    if (lane == 0 && gmask) wbase = atomicAdd(&s_ng, (unsigned)__popc(gmask));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (gated) {
+      const int pos = (int)wbase + __popc(gmask & ((1u << lane) - 1u));
       s_pid[pos] = (unsigned short)(row * kTileW + lane);
-      s_z[pos] = zk[k];
-      s_c[pos] = ck[k];
+      s_z[pos] = Depth<DT>::z(Dk[k]);
+      s_c[pos] = ckv[k];
       s_rgb[pos] = rgbk[k];
     }
   }
@@ -563,26 +539,33 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   const int n_g = (int)s_ng;
   const CamDev& C = bc.cam;
 
-  // (a) + (b): back-project, consistency, weight; coarse cell of each gated point
-  float r[2][3];
+  // (a) Eq. 8, (b) Eq. 4-7 and 10, (c) Sec. II.5(1)d-e for each gated point
   bool has[2] = {false, false};
   float mu[2] = {0.0f, 0.0f};
   int mexp[2] = {0, 0};
   unsigned cord[2] = {0u, 0u};
   int hpos[2] = {0, 0};
   long long gi[2] = {0, 0};
+  float frac[2][3];
+  unsigned long long fkey[2] = {kKeyEmpty, kKeyEmpty};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int i = threadIdx.x + j * kThreads;
     if (i >= n_g) continue;
     const int pid = s_pid[i];
-    const int x = tx * kTileW + (pid & (kTileW - 1)), y = ty * kTileH + pid / kTileW;
-    gi[j] = C.off + (long long)y * W + x;
+    const int x = td.x0 + (pid & (kTileW - 1)), y = td.y0 + pid / kTileW;
+    gi[j] = td.off + (long long)y * W + x;
     const float z = s_z[i];
     const float c = s_c[i];
     const float2 rx = __ldg(rays + C.ray_x + x), ry = __ldg(rays + C.ray_y + y);
-    float P[3];
+    float P[3], r[3];
     world_point(C, z, rx.x, ry.x, P);                                 // Eq. 8
+    has[j] = grid_coords(rig, P, r);
+    // start the lookup of the coarse cell's level and slot range (Sec. II.5(1)d)
+    const unsigned long long ck = has[j] ? coarse_key(r) : kKeyEmpty;
+    unsigned ch = 0u;
+    ulonglong2 ce = make_ulonglong2(kKeyEmpty, 0ull);
+    if (has[j]) ce = coarse_probe(t, ck, ch);
     float sh = 0.0f, sl = 0.0f, eh = 0.0f, el = 0.0f;
     int nview = 0;
     if (rig.use_cons && k1 > 0) {
@@ -607,7 +590,6 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     mu[j] = __fmul_rn(__fmul_rn(base, expf(-fh)), __fsub_rn(1.0f, fl));
     mexp[j] = m;
     cord[j] = ordered(c);
-    has[j] = grid_coords(rig, P, r[j]);
     if (trace) {
       if (tr.pw) {
         tr.pw[3 * gi[j] + 0] = P[0] * unit_m;
@@ -617,49 +599,31 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       if (tr.e) tr.e[gi[j]] = eh;
       if (tr.omega) tr.omega[gi[j]] = ldexpf(mu[j], -m);
       if (tr.nview) tr.nview[gi[j]] = nview;
-      if (tr.key && !has[j]) tr.key[gi[j]] = kKeyEmpty;
     }
     if (has[j]) {
-      hpos[j] = local_pos<kAssignCS>(s_ck, kKeyEmpty, coarse_key(r[j]));
-      if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrCoarseFull); }
-    }
-  }
-  __syncthreads();
-  // (c) Sec. II.5(1)d: level and slot range of each coarse cell present in the tile
-  for (int i = threadIdx.x; i < kAssignCS; i += kThreads) {
-    const unsigned long long ck = s_ck[i];
-    if (ck == kKeyEmpty) continue;
-    const unsigned cs = coarse_find(t, ck);
-    s_cl[i] = cs != kSlotNone ? __ldcg(&t.clevel[cs]) : 0u;
-    s_cb[i] = cs != kSlotNone ? __ldcg(&t.cbase[cs]) : kSlotNone;
-  }
-  __syncthreads();
-  // (c) Sec. II.5(1)e: cell key, its dense slot, and the point's offset inside the cell
-  float frac[2][3];
-  unsigned long long fkey[2] = {kKeyEmpty, kKeyEmpty};
+      // Sec. II.5(1)e: cell key, its dense slot, and the point's offset inside the cell
+      const unsigned lb = coarse_lvbase(t, ck, ch, ce);
+      const int l = (int)(lb >> 27);
+      const unsigned cbase = lb & kBaseNone;
+      const unsigned long long fk = fine_key(r, l);
+      const int kk[3] = {(int)((fk >> 40) & 0xfffff) - kKeyBias, (int)((fk >> 20) & 0xfffff) - kKeyBias,
+                         (int)(fk & 0xfffff) - kKeyBias};
+      const float sl2 = pow2f(l);
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    if (!has[j]) continue;
-    const int l = (int)s_cl[hpos[j]];
-    const unsigned base = s_cb[hpos[j]];
-    const unsigned long long fk = fine_key(r[j], l);
-    const int kk[3] = {(int)((fk >> 40) & 0xfffff) - kKeyBias, (int)((fk >> 20) & 0xfffff) - kKeyBias,
-                       (int)(fk & 0xfffff) - kKeyBias};
-    const float sl = pow2f(l);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) frac[j][a] = __fsub_rn(__fmul_rn(r[j][a], sl), (float)kk[a]);
-    // sub-cell of the coarse cell: k - (coarse << l) = k & (2^l - 1)
-    const unsigned mask = (1u << l) - 1u;
-    const unsigned local = ((((unsigned)kk[0] & mask) << l | ((unsigned)kk[1] & mask)) << l) |
-                           ((unsigned)kk[2] & mask);
-    if (base == kSlotNone) {                    // slot capacity exceeded (reported)
-      has[j] = false;
-    } else {
-      fkey[j] = fk;
-      hpos[j] = local_pos<kAssignTS>(s_fk, kSlotNone, base + local);
-      if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrSlots); }
+      for (int a = 0; a < 3; ++a) frac[j][a] = __fsub_rn(__fmul_rn(r[a], sl2), (float)kk[a]);
+      // sub-cell of the coarse cell: k - (coarse << l) = k & (2^l - 1)
+      const unsigned mask = (1u << l) - 1u;
+      const unsigned local = ((((unsigned)kk[0] & mask) << l | ((unsigned)kk[1] & mask)) << l) |
+                             ((unsigned)kk[2] & mask);
+      if (cbase == kBaseNone) {                 // slot capacity exceeded (reported)
+        has[j] = false;
+      } else {
+        fkey[j] = fk;
+        hpos[j] = local_pos<kAssignTS>(s_fk, kSlotNone, cbase + local);
+        if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrSlots); }
+      }
     }
-    if (trace && tr.key) tr.key[gi[j]] = has[j] ? fk : kKeyEmpty;
+    if (trace && tr.key) tr.key[gi[j]] = has[j] ? fkey[j] : kKeyEmpty;
   }
   __syncthreads();
   // compact the tile's cells: entry index per hash position
@@ -677,6 +641,10 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
   }
   __syncthreads();
+  // reserve the tile's partial records now; the index is needed only at the end
+  const unsigned n_local = s_n;
+  unsigned base_pi = 0u;
+  if (threadIdx.x == 0) base_pi = atomicAdd(&t.cnt->n_partials, n_local);
   // (d) Sec. II.5(2)a: members, largest C, smallest weight exponent
   int ent[2] = {0, 0};
 #pragma unroll
@@ -712,11 +680,9 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], (unsigned)(q[a] >> kLoBits));
     }
   }
+  if (threadIdx.x == 0) s_base = base_pi;
   __syncthreads();
   // one partial record per (tile, cell); the link step files it under its cell
-  const unsigned n_local = s_n;
-  if (threadIdx.x == 0) s_base = atomicAdd(&t.cnt->n_partials, n_local);
-  __syncthreads();
   for (int e = threadIdx.x; e < (int)n_local; e += kThreads) {
     const unsigned pi = s_base + (unsigned)e;
     if (pi >= t.max_partials) { atomicOr(&t.cnt->error, kErrPartials); continue; }
@@ -807,8 +773,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
     }
     if (i < n_coarse) {
       const unsigned cs = t.cused[i];
-      t.ckey[cs] = kKeyEmpty;
-      t.ccount[cs] = 0u;
+      t.coarse[cs].key = kKeyEmpty;
+      t.coarse[cs].count = 0u;
     }
   }
 }
@@ -968,8 +934,8 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
       t.fmmin[i] = INT_MAX;
     }
     if (i < ccap) {
-      t.ckey[i] = kKeyEmpty;
-      t.ccount[i] = 0u;
+      t.coarse[i].key = kKeyEmpty;
+      t.coarse[i].count = 0u;
     }
   }
 }
@@ -993,8 +959,7 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x,
                                                                        geo.count_chunks);
   mark(2);
-  k_assign<DT><<<dim3(geo.tiles_max, geo.n_cams), kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr,
-                                                                                (float)out.unit_m);
+  k_assign<DT><<<t.n_tiles, kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr, (float)out.unit_m);
   mark(3);
   k_link<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(4);
@@ -1008,6 +973,38 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
 }
 
 }  // namespace
+
+int n_tiles_for(const RigDev& rig) {
+  int n = 0;
+  for (int i = 0; i < rig.n_cams; ++i)
+    n += ((rig.cam[i].W + kTileW - 1) / kTileW) * ((rig.cam[i].H + kTileH - 1) / kTileH);
+  return n;
+}
+
+void fill_tiles(const RigDev& rig, TileDesc* out) {
+  int n = 0;
+  for (int i = 0; i < rig.n_cams; ++i) {
+    const CamDev& c = rig.cam[i];
+    for (int y0 = 0; y0 < c.H; y0 += kTileH)
+      for (int x0 = 0; x0 < c.W; x0 += kTileW) {
+        TileDesc d;
+        d.cam = i; d.x0 = x0; d.y0 = y0; d.W = c.W; d.H = c.H; d.k1 = rig.k1; d.off = c.off;
+        out[n++] = d;
+      }
+  }
+}
+
+void fill_block_consts(const RigDev& rig, BlockConst* out) {
+  for (int i = 0; i < rig.n_cams; ++i) {
+    BlockConst& b = out[i];
+    memset(&b, 0, sizeof(b));
+    b.cam = rig.cam[i];
+    for (int q = 0; q < rig.k1; ++q) {
+      b.pair[q] = rig.pair[rig.cam[i].pair0 + q];
+      b.nb[q] = rig.cam[b.pair[q].j];
+    }
+  }
+}
 
 cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cudaStream_t s) {
   k_init_tables<<<1024, 256, 0, s>>>(t, fcap, ccap);
