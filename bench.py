@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "depth px/s and frames/s at 8x1280x720 views; p50/p99 latency, served vs plain"
-KERNELS_PER_FRAME = 5      # count, assign, reduce, scan, emit
+KERNELS_PER_FRAME = 6      # count, levels, assign, reduce, scan, emit
 CELL_OUT_BYTES = 44        # pos 12 + rgb 12 + weight 4 + count 4 + rep 4 + key 8
 
 

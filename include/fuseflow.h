@@ -161,8 +161,8 @@ int fuseflow_get_neighbours(const fuseflow_ctx *ctx, int32_t *out, int32_t *k_mi
  * fuseflow_read_stage_times waits for the last recorded event, writes the summed
  * milliseconds of each of the FUSEFLOW_N_STAGES stages to ms[] and the number of frames
  * to *n_frames, then resets the ring.  Stages: 0 clear, 1 count (a, c2), 2 assign
- * (b, c, d per tile), 3 link (hash insertion), 4 reduce (d per cell), 5 scan, 6 emit. */
-#define FUSEFLOW_N_STAGES 7
+ * (b, c, d per tile), 3 reduce (d per cell), 4 scan, 5 emit. */
+#define FUSEFLOW_N_STAGES 6
 int fuseflow_enable_stage_timing(fuseflow_ctx *ctx, int enable);
 int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
 const char *fuseflow_stage_name(int stage);
@@ -182,11 +182,12 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
  * change the process's memory footprint after start-up.  This call needs no context: it
  * takes the rig and parameters directly, calls no cudaMalloc, cudaFree or other
  * allocating routine (device or host), and keeps all of its scratch in one file-scope
- * device array of about 21 MiB that every GPU loading this library holds until exit.
+ * device array of about 26 MiB that every GPU loading this library holds until exit.
  *
  * Limits: at most 524,288 pixels per frame over all cameras, at most 65,536 ray-table
- * entries (sum over cameras of width + height), and max_cells <= 32,768 (0 selects
- * 32,768); larger requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.  A
+ * entries (sum over cameras of width + height), 2 (K - 1) times that at most 393,216
+ * (K = min(k_views, n_cams)), and max_cells <= 32,768 (0 selects 32,768); larger
+ * requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.  A
  * frame that produces more than 131,072 (tile, cell) partial records reports a capacity
  * error in stats->error.
  * Inputs are device pointers as for fuseflow_fuse_frame; pos[3*max_cells],

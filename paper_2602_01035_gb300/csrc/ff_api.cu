@@ -143,6 +143,93 @@ int validate(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr, i
   return FUSEFLOW_OK;
 }
 
+// Rig constants shared by fuseflow_create and the static entry point: per-camera
+// intrinsics and poses, the ray tables rx(x) = (x - cx)/fx and ry(y) = (y - cy)/fy as ff,
+// the relative poses of Eq. 4 (T_ji = T_j T_i^-1) and the separable pair rays.
+// `rays` holds sum(W + H) entries and `pray` 2 k1 sum(W + H) float4.
+void build_rig(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr, int n_cams,
+               const fuseflow_params* params, const int32_t* nbr, int k1, RigDev& rig,
+               float2* rays, float4* pray) {
+  const double unit = params->depth_scale;
+  std::memset(&rig, 0, sizeof(rig));
+  rig.n_cams = n_cams;
+  rig.k1 = k1;
+  rig.tau = params->tau;
+  rig.use_conf = params->use_conf ? 1 : 0;
+  rig.use_cons = params->use_consistency ? 1 : 0;
+  rig.max_level = params->max_level;
+  rig.n_min = params->n_min;
+  rig.inv_s0u = (float)(unit / params->coarse_cell_m);
+  const double sig_u = params->sigma_m / unit;
+  if (k1 > 0) split(1.0 / (sig_u * sig_u * k1), rig.einv_h, rig.einv_l);
+  rig.depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
+  int nr = 0, np = 0;
+  long long off = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    const fuseflow_intrinsics& k = intr[i];
+    const fuseflow_extrinsics& e = extr[i];
+    CamDev& c = rig.cam[i];
+    c.W = k.width;
+    c.H = k.height;
+    c.off = off;
+    off += (long long)k.width * k.height;
+    c.fx = (float)k.fx; c.fy = (float)k.fy; c.cx = (float)k.cx; c.cy = (float)k.cy;
+    split(k.fx, c.fxh, c.fxl);
+    split(k.fy, c.fyh, c.fyl);
+    split(k.cx, c.cxh, c.cxl);
+    split(k.cy, c.cyh, c.cyl);
+    double cen[3], ax[3];
+    centre_axis(e, cen, ax);
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) c.Rwc[3 * r + q] = (float)e.R[3 * q + r];
+      c.cwc[r] = (float)(cen[r] / unit);
+    }
+    c.ray_x = nr;
+    for (int x = 0; x < k.width; ++x, ++nr) split(((double)x - k.cx) / k.fx, rays[nr].x, rays[nr].y);
+    c.ray_y = nr;
+    for (int y = 0; y < k.height; ++y, ++nr) split(((double)y - k.cy) / k.fy, rays[nr].x, rays[nr].y);
+    c.pair0 = i * k1;
+    for (int q = 0; q < k1; ++q) {
+      const int j = nbr[i * k1 + q];
+      const fuseflow_extrinsics& ej = extr[j];
+      PairDev& P = rig.pair[c.pair0 + q];
+      P.j = j;
+      double Rji[9], tji[3];
+      for (int r = 0; r < 3; ++r)
+        for (int s2 = 0; s2 < 3; ++s2) {
+          double acc = 0;
+          for (int m = 0; m < 3; ++m) acc += ej.R[3 * r + m] * e.R[3 * s2 + m];   // R_j R_i^T
+          Rji[3 * r + s2] = acc;
+        }
+      for (int r = 0; r < 3; ++r)
+        tji[r] = ej.t[r] - (Rji[3 * r] * e.t[0] + Rji[3 * r + 1] * e.t[1] + Rji[3 * r + 2] * e.t[2]);
+      for (int a = 0; a < 9; ++a) split(Rji[a], P.Rh[a], P.Rl[a]);
+      for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
+      // separable pair rays A_k(x) = R[k][0] rx(x) + R[k][2], B_k(y) = R[k][1] ry(y)
+      auto put = [&](double v0, double v1, double v2) {
+        float4& u = pray[np++];
+        float4& w = pray[np++];
+        split(v0, u.x, u.y);
+        split(v1, u.z, u.w);
+        split(v2, w.x, w.y);
+        w.z = 0.0f;
+        w.w = 0.0f;
+      };
+      P.ga = np;
+      for (int x = 0; x < k.width; ++x) {
+        const double rx = ((double)x - k.cx) / k.fx;
+        put(Rji[0] * rx + Rji[2], Rji[3] * rx + Rji[5], Rji[6] * rx + Rji[8]);
+      }
+      P.gb = np;
+      for (int y = 0; y < k.height; ++y) {
+        const double ry = ((double)y - k.cy) / k.fy;
+        put(Rji[1] * ry, Rji[4] * ry, Rji[7] * ry);
+      }
+    }
+  }
+  rig.n_px = off;
+}
+
 }  // namespace
 
 extern "C" {
@@ -213,75 +300,15 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   // ---------------------------------------------------------------- rig constants
   RigDev* rig = new (std::nothrow) RigDev();
   if (!rig) { delete ctx; return FUSEFLOW_ERR_OUT_OF_MEMORY; }
-  rig->n_cams = n_cams;
-  rig->k1 = ctx->k1;
-  rig->tau = params->tau;
-  rig->use_conf = params->use_conf ? 1 : 0;
-  rig->use_cons = params->use_consistency ? 1 : 0;
-  rig->max_level = params->max_level;
-  rig->n_min = params->n_min;
-  rig->inv_s0u = (float)(unit / params->coarse_cell_m);
-  const double sig_u = params->sigma_m / unit;
-  if (ctx->k1 > 0) split(1.0 / (sig_u * sig_u * ctx->k1), rig->einv_h, rig->einv_l);
-  rig->depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
-  std::vector<float2> rays;
-  long long off = 0;
-  int max_w = 0, max_h = 0;
-  long long max_px = 0;
+  long long off = 0, n_rays = 0, max_px = 0;
   for (int i = 0; i < n_cams; ++i) {
-    const fuseflow_intrinsics& k = intr[i];
-    const fuseflow_extrinsics& e = extr[i];
-    CamDev& c = rig->cam[i];
-    c.W = k.width;
-    c.H = k.height;
-    c.off = off;
-    off += (long long)k.width * k.height;
-    max_w = std::max(max_w, k.width);
-    max_h = std::max(max_h, k.height);
-    max_px = std::max(max_px, (long long)k.width * k.height);
-    c.fx = (float)k.fx; c.fy = (float)k.fy; c.cx = (float)k.cx; c.cy = (float)k.cy;
-    split(k.fx, c.fxh, c.fxl);
-    split(k.fy, c.fyh, c.fyl);
-    split(k.cx, c.cxh, c.cxl);
-    split(k.cy, c.cyh, c.cyl);
-    double cen[3], ax[3];
-    centre_axis(e, cen, ax);
-    for (int r = 0; r < 3; ++r) {
-      for (int q = 0; q < 3; ++q) c.Rwc[3 * r + q] = (float)e.R[3 * q + r];
-      c.cwc[r] = (float)(cen[r] / unit);
-    }
-    c.ray_x = (int)rays.size();
-    for (int x = 0; x < k.width; ++x) {
-      float2 f;
-      split(((double)x - k.cx) / k.fx, f.x, f.y);
-      rays.push_back(f);
-    }
-    c.ray_y = (int)rays.size();
-    for (int y = 0; y < k.height; ++y) {
-      float2 f;
-      split(((double)y - k.cy) / k.fy, f.x, f.y);
-      rays.push_back(f);
-    }
-    c.pair0 = i * ctx->k1;
-    for (int q = 0; q < ctx->k1; ++q) {
-      const int j = ctx->nbr[(size_t)i * ctx->k1 + q];
-      const fuseflow_extrinsics& ej = extr[j];
-      PairDev& P = rig->pair[c.pair0 + q];
-      P.j = j;
-      double Rji[9], tji[3];
-      for (int r = 0; r < 3; ++r)
-        for (int s = 0; s < 3; ++s) {
-          double acc = 0;
-          for (int m = 0; m < 3; ++m) acc += ej.R[3 * r + m] * e.R[3 * s + m];   // R_j R_i^T
-          Rji[3 * r + s] = acc;
-        }
-      for (int r = 0; r < 3; ++r)
-        tji[r] = ej.t[r] - (Rji[3 * r] * e.t[0] + Rji[3 * r + 1] * e.t[1] + Rji[3 * r + 2] * e.t[2]);
-      for (int a = 0; a < 9; ++a) split(Rji[a], P.Rh[a], P.Rl[a]);
-      for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
-    }
+    off += (long long)intr[i].width * intr[i].height;
+    n_rays += intr[i].width + intr[i].height;
+    max_px = std::max(max_px, (long long)intr[i].width * intr[i].height);
   }
-  rig->n_px = off;
+  std::vector<float2> rays((size_t)n_rays);
+  std::vector<float4> pray((size_t)std::max<long long>(1, 2 * ctx->k1 * n_rays));
+  build_rig(intr, extr, n_cams, params, ctx->nbr.data(), ctx->k1, *rig, rays.data(), pray.data());
   ctx->n_px = off;
   ctx->max_cells = params->max_cells > 0 ? params->max_cells : std::max<long long>(65536, off / 8);
   // A coarse cell at level l >= 1 holds n_c >= n_min 4^l points, so its 8^l dense slots are
@@ -296,12 +323,12 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   {
-    // several 1024-pixel chunks per count block: about two waves of 4 blocks per SM
+    // several 2048-pixel chunks per count block: one wave of 3 blocks per SM
     long long total_chunks = 0;
-    for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 1023) / 1024;
-    const long long per = total_chunks / (2ll * 4 * sms);
+    for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 2047) / 2048;
+    const long long per = (total_chunks + 3ll * sms - 1) / (3ll * sms);
     ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
-    const long long max_chunks = (max_px + 1023) / 1024;
+    const long long max_chunks = (max_px + 2047) / 2048;
     ctx->geo.count_blocks_x = (int)((max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
   int tiles_max = 0;
@@ -344,13 +371,11 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const size_t q_key = take_out(sizeof(unsigned long long) * (size_t)ctx->max_cells);
   ctx->out_bytes = po;
 
-  const int n_tiles = n_tiles_for(*rig);
-  std::vector<TileDesc> tiles((size_t)n_tiles);
+  const int n_tiles = fill_tile_index(*rig, &ctx->geo.tiles);
   std::vector<BlockConst> bconst((size_t)n_cams);
-  fill_tiles(*rig, tiles.data());
   fill_block_consts(*rig, bconst.data());
-  const size_t tiles_bytes = align_up(sizeof(TileDesc) * (size_t)n_tiles, 256);
-  const size_t blocks_bytes = tiles_bytes + sizeof(BlockConst) * (size_t)n_cams;
+  const size_t pray_at = align_up(sizeof(BlockConst) * (size_t)n_cams, 256);
+  const size_t blocks_bytes = pray_at + sizeof(float4) * pray.size();
   if (cudaMalloc(&ctx->d_rig, sizeof(RigDev)) != cudaSuccess ||
       cudaMalloc(&ctx->d_rays, sizeof(float2) * rays.size()) != cudaSuccess ||
       cudaMalloc(&ctx->d_blocks, blocks_bytes) != cudaSuccess ||
@@ -369,8 +394,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     t.coarse = reinterpret_cast<CoarseEntry*>(b + o_coarse);
     t.n_min = params->n_min;
     t.max_level = params->max_level;
-    t.tiles = static_cast<const TileDesc*>(ctx->d_blocks);
-    t.bconst = reinterpret_cast<const BlockConst*>(static_cast<char*>(ctx->d_blocks) + tiles_bytes);
+    t.bconst = static_cast<const BlockConst*>(ctx->d_blocks);
+    t.pray = reinterpret_cast<const float4*>(static_cast<char*>(ctx->d_blocks) + pray_at);
     t.n_tiles = n_tiles;
     t.cused = reinterpret_cast<unsigned*>(b + o_cused);
     t.cmask = ctx->ccap - 1;
@@ -400,9 +425,10 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     od.unit_m = unit;
     if (cudaMemcpy(ctx->d_rig, rig, sizeof(RigDev), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_rays, rays.data(), sizeof(float2) * rays.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(ctx->d_blocks, tiles.data(), sizeof(TileDesc) * (size_t)n_tiles, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(static_cast<char*>(ctx->d_blocks) + tiles_bytes, bconst.data(),
-                   sizeof(BlockConst) * (size_t)n_cams, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_blocks, bconst.data(), sizeof(BlockConst) * (size_t)n_cams,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(static_cast<char*>(ctx->d_blocks) + pray_at, pray.data(), sizeof(float4) * pray.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->d_tables, 0, ctx->table_bytes) != cudaSuccess ||
         cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
         launch_init_tables(t, ctx->max_slots, ctx->ccap, 0) != cudaSuccess ||
@@ -582,8 +608,8 @@ int fuseflow_read_stage_times(fuseflow_ctx* ctx, double* ms, int64_t* n_frames) 
 }
 
 const char* fuseflow_stage_name(int stage) {
-  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "link", "reduce",
-                                                 "scan", "emit"};
+  static const char* names[FUSEFLOW_N_STAGES] = {"clear", "count", "assign", "reduce", "scan",
+                                                 "emit"};
   return (stage >= 0 && stage < FUSEFLOW_N_STAGES) ? names[stage] : "unknown";
 }
 
@@ -614,18 +640,18 @@ constexpr long long kStaticMaxCells = 1ll << 15;       // 32,768 output cells
 constexpr unsigned kStaticSlots = 1u << 18;            // dense cell slots
 constexpr unsigned kStaticCoarse = 1u << 16;           // coarse hash slots
 constexpr int kStaticMaxRays = 1 << 16;                // sum over cameras of W + H
-constexpr int kStaticMaxTiles = (int)(kStaticMaxPixels / 512) + 4 * kMaxCams;   // 32x16 tiles
+constexpr int kStaticMaxPairRays = 6 * kStaticMaxRays;  // float4: 2 (K - 1) sum(W + H)
 constexpr long long kStaticWords = kStaticMaxPixels / 32;
 constexpr int kStaticWBlocks = (int)((kStaticWords + 1023) / 1024);
-constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 1024 + 1);   // chunks = 1
+constexpr int kStaticBStats = kMaxCams * (int)(kStaticMaxPixels / 2048 + 1);   // chunks = 1
 constexpr int kStaticMaxDevices = 64;
 
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kSRig = 0;
 constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
-constexpr size_t kSTiles = al256(kSRays + sizeof(float2) * kStaticMaxRays);
-constexpr size_t kSBConst = al256(kSTiles + sizeof(TileDesc) * kStaticMaxTiles);
-constexpr size_t kSFKey = al256(kSBConst + sizeof(BlockConst) * kMaxCams);
+constexpr size_t kSBConst = al256(kSRays + sizeof(float2) * kStaticMaxRays);
+constexpr size_t kSPRay = al256(kSBConst + sizeof(BlockConst) * kMaxCams);
+constexpr size_t kSFKey = al256(kSPRay + sizeof(float4) * kStaticMaxPairRays);
 constexpr size_t kSFHead = al256(kSFKey + sizeof(unsigned long long) * kStaticSlots);
 constexpr size_t kSFMmin = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSFused = al256(kSFMmin + sizeof(int) * kStaticSlots);
@@ -639,7 +665,7 @@ constexpr size_t kSStaged = al256(kSPNext + sizeof(unsigned) * kStaticMaxPartial
 constexpr size_t kSWPre = al256(kSStaged + sizeof(CellOut) * kStaticMaxCells);
 constexpr size_t kSBSum = al256(kSWPre + sizeof(unsigned) * kStaticWords);
 constexpr size_t kStaticBytes = al256(kSBSum + sizeof(unsigned) * kStaticWBlocks);
-static_assert(kStaticBytes <= (24u << 20), "static scratch must stay modest");
+static_assert(kStaticBytes <= (32u << 20), "static scratch must stay modest");
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -647,7 +673,7 @@ std::mutex g_static_mutex;                             // guards the host stagin
 unsigned char* g_static_dev[kStaticMaxDevices] = {};   // device address per device
 RigDev g_static_rig;                                   // host staging of the rig constants
 float2 g_static_rays[kStaticMaxRays];                  // host staging of the ray tables
-TileDesc g_static_tiles[kStaticMaxTiles];              // host staging of the tile list
+float4 g_static_pray[kStaticMaxPairRays];              // host staging of the pair rays
 BlockConst g_static_bconst[kMaxCams];                  // host staging of the block constants
 
 // The neighbour rule of neighbour_table() above (Sec. II.5(2)b: optical-axis angle, then
@@ -752,11 +778,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
     if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
   }
   const long long max_cells = params->max_cells > 0 ? params->max_cells : kStaticMaxCells;
-  int n_tiles_req = 0;
-  for (int i = 0; i < n_cams; ++i)
-    n_tiles_req += ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16);
-  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells ||
-      n_tiles_req > kStaticMaxTiles)
+  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells)
     return FUSEFLOW_ERR_CAPACITY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
@@ -774,81 +796,27 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   int32_t nbr[kMaxCams * kMaxK1];
   neighbour_table_fixed(extr, n_cams, k1, nbr);
   const double unit = params->depth_scale;
+  if (2ll * k1 * n_rays > kStaticMaxPairRays) return FUSEFLOW_ERR_CAPACITY;
   RigDev& rig = g_static_rig;
-  std::memset(&rig, 0, sizeof(rig));
-  rig.n_cams = n_cams;
-  rig.k1 = k1;
-  rig.tau = params->tau;
-  rig.use_conf = params->use_conf ? 1 : 0;
-  rig.use_cons = params->use_consistency ? 1 : 0;
-  rig.max_level = params->max_level;
-  rig.n_min = params->n_min;
-  rig.inv_s0u = (float)(unit / params->coarse_cell_m);
-  const double sig_u = params->sigma_m / unit;
-  if (k1 > 0) split(1.0 / (sig_u * sig_u * k1), rig.einv_h, rig.einv_l);
-  rig.depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
-  rig.n_px = n_px;
-  int nr = 0;
-  long long off = 0;
-  for (int i = 0; i < n_cams; ++i) {
-    const fuseflow_intrinsics& k = intr[i];
-    const fuseflow_extrinsics& e = extr[i];
-    CamDev& c = rig.cam[i];
-    c.W = k.width;
-    c.H = k.height;
-    c.off = off;
-    off += (long long)k.width * k.height;
-    c.fx = (float)k.fx; c.fy = (float)k.fy; c.cx = (float)k.cx; c.cy = (float)k.cy;
-    split(k.fx, c.fxh, c.fxl);
-    split(k.fy, c.fyh, c.fyl);
-    split(k.cx, c.cxh, c.cxl);
-    split(k.cy, c.cyh, c.cyl);
-    double cen[3], ax[3];
-    centre_axis(e, cen, ax);
-    for (int r = 0; r < 3; ++r) {
-      for (int q = 0; q < 3; ++q) c.Rwc[3 * r + q] = (float)e.R[3 * q + r];
-      c.cwc[r] = (float)(cen[r] / unit);
-    }
-    c.ray_x = nr;
-    for (int x = 0; x < k.width; ++x, ++nr) split(((double)x - k.cx) / k.fx, g_static_rays[nr].x, g_static_rays[nr].y);
-    c.ray_y = nr;
-    for (int y = 0; y < k.height; ++y, ++nr) split(((double)y - k.cy) / k.fy, g_static_rays[nr].x, g_static_rays[nr].y);
-    c.pair0 = i * k1;
-    for (int q = 0; q < k1; ++q) {
-      const int j = nbr[i * k1 + q];
-      const fuseflow_extrinsics& ej = extr[j];
-      PairDev& P = rig.pair[c.pair0 + q];
-      P.j = j;
-      double Rji[9], tji[3];
-      for (int r = 0; r < 3; ++r)
-        for (int s2 = 0; s2 < 3; ++s2) {
-          double acc = 0;
-          for (int m = 0; m < 3; ++m) acc += ej.R[3 * r + m] * e.R[3 * s2 + m];
-          Rji[3 * r + s2] = acc;
-        }
-      for (int r = 0; r < 3; ++r)
-        tji[r] = ej.t[r] - (Rji[3 * r] * e.t[0] + Rji[3 * r + 1] * e.t[1] + Rji[3 * r + 2] * e.t[2]);
-      for (int a = 0; a < 9; ++a) split(Rji[a], P.Rh[a], P.Rl[a]);
-      for (int a = 0; a < 3; ++a) split(tji[a] / unit, P.th[a], P.tl[a]);
-    }
-  }
-  const int n_tiles = n_tiles_for(rig);
-  fill_tiles(rig, g_static_tiles);
+  build_rig(intr, extr, n_cams, params, nbr, k1, rig, g_static_rays, g_static_pray);
+  const int nr = (int)n_rays;
+  const int np = (int)(2ll * k1 * n_rays);
+  Geometry geo{};
+  const int n_tiles = fill_tile_index(rig, &geo.tiles);
   fill_block_consts(rig, g_static_bconst);
   // pageable host -> device copies return once the host buffers have been read
-  if (cudaMemcpyAsync(base + kSTiles, g_static_tiles, sizeof(TileDesc) * (size_t)n_tiles,
-                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + kSBConst, g_static_bconst, sizeof(BlockConst) * (size_t)n_cams,
+  if (cudaMemcpyAsync(base + kSBConst, g_static_bconst, sizeof(BlockConst) * (size_t)n_cams,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + kSRig, &rig, sizeof(RigDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + kSRays, g_static_rays, sizeof(float2) * (size_t)nr, cudaMemcpyHostToDevice,
-                      s) != cudaSuccess)
+                      s) != cudaSuccess ||
+      (np > 0 && cudaMemcpyAsync(base + kSPRay, g_static_pray, sizeof(float4) * (size_t)np,
+                                 cudaMemcpyHostToDevice, s) != cudaSuccess))
     return FUSEFLOW_ERR_CUDA;
 
-  Geometry geo{};
   geo.n_cams = n_cams;
   geo.depth_f32 = rig.depth_f32;
-  geo.count_blocks_x = (int)((max_px + 1023) / 1024);
+  geo.count_blocks_x = (int)((max_px + 2047) / 2048);
   geo.count_chunks = 1;
   geo.tiles_max = tiles_max;
   int sms = 152;
@@ -857,8 +825,8 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
   t.n_min = params->n_min;
   t.max_level = params->max_level;
-  t.tiles = reinterpret_cast<const TileDesc*>(base + kSTiles);
   t.bconst = reinterpret_cast<const BlockConst*>(base + kSBConst);
+  t.pray = reinterpret_cast<const float4*>(base + kSPRay);
   t.n_tiles = n_tiles;
   OutDev od{};
   od.stats = stats;

@@ -23,7 +23,6 @@ constexpr uint32_t kSlotNone = 0xffffffffu;
 constexpr int kFixShift = 36;            // per-cell fixed point: largest member weight ~ 2^36
 constexpr int kKeyBias = 1 << 19;        // cell index range [-2^19, 2^19) per axis
 constexpr float kTieBandPx = 4e-3f;      // float32 projection error bound (pixels), generous
-constexpr float kZGuard = 1.0f;          // |a_z| below one depth unit: use the ff value
 
 // error bits of FrameCounters::error
 constexpr unsigned kErrSlots = 1u;       // the cells' dense slot ranges exceed the slot capacity
@@ -50,7 +49,11 @@ struct PairDev {                 // camera i -> neighbour j: a = R_ji p_c + t_ji
   float Rh[9], Rl[9];            // R_ji = R_j R_i^T as ff
   float th[3], tl[3];            // t_ji = t_j - R_ji t_i as ff (depth units)
   int j;
-  int pad[3];
+  // separable pair rays: with p_c = z (rx(x), ry(y), 1), R_ji p_c = z (A(x) + B(y)),
+  // A_k(x) = R_ji[k][0] rx(x) + R_ji[k][2] and B_k(y) = R_ji[k][1] ry(y), each stored as
+  // ff in two float4 per column / row: (A0h, A0l, A1h, A1l), (A2h, A2l, 0, 0)
+  int ga, gb;                    // float4 index of column 0's A and row 0's B
+  int pad;
 };
 
 struct RigDev {
@@ -75,11 +78,13 @@ struct BlockConst {
   CamDev nb[kMaxK1];
 };
 
-// One 32x16 tile of one camera (the assign step's unit of work).
-struct __align__(32) TileDesc {
-  int cam, x0, y0, W;
-  int H, k1;
-  long long off;                 // global index of the camera's pixel (0, 0)
+// Where the assign step's tiles are: camera i owns tiles [first[i], first[i+1]), row-major
+// over its ceil(W/32) x ceil(H/16) grid.  Passed by value (constant bank) to the kernel.
+struct TileIndex {
+  int n_cams, k1;
+  int first[kMaxCams + 1];
+  int W[kMaxCams], H[kMaxCams];
+  long long off[kMaxCams];       // global index of each camera's pixel (0, 0)
 };
 
 // Per (tile, cell) partial result of the assign step; the link step pushes it onto its
@@ -125,9 +130,8 @@ struct FrameCounters {           // zeroed before every frame
   unsigned bmin_inv[3];          // ~ordered(min): max-reduced so that zero is neutral
   unsigned bmax[3];              // ordered(max)
   unsigned scan_done;            // blocks of the scan step that have finished
-  unsigned count_done;           // blocks of the count step that have finished
-  unsigned n_slots;              // dense cell slots in use (sum over coarse cells of 8^l)
   unsigned pad;
+  unsigned long long n_slots;    // dense cell slots claimed (sum over coarse cells of 8^l)
 };
 
 struct BlockStats {              // per block of the coarse-count step
@@ -201,6 +205,19 @@ __device__ __forceinline__ void ff_affine_row(const float* Rh, const float* Rl, 
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, q1)),
                              __fadd_rn(__fadd_rn(q2, q3), tl));
   fast_two_sum(s, lo, oh, ol);
+}
+
+// One component of a = z (A + B) + t in ff (A, B, t as ff, z exact); the result (oh, ol)
+// is not renormalised (|ol| stays within a few ulp of oh, unless z(A + B) and t cancel).
+__device__ __forceinline__ void ff_ray_affine(float Ah, float Al, float Bh, float Bl, float z,
+                                              float th, float tl, float& oh, float& ol) {
+  float gh, ge, p, pe, e;
+  two_sum(Ah, Bh, gh, ge);
+  ge = __fadd_rn(ge, __fadd_rn(Al, Bl));
+  two_prod(z, gh, p, pe);
+  pe = __fmaf_rn(z, ge, pe);
+  two_sum(p, th, oh, e);
+  ol = __fadd_rn(e, __fadd_rn(pe, tl));
 }
 
 // --------------------------------------------------------------------------- depth decode

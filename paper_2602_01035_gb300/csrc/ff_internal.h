@@ -39,8 +39,8 @@ struct Tables {                  // context-owned device scratch
   long long n_words;
   int n_wblocks;
   int n_min, max_level;          // level rule (Sec. II.5(1)d)
-  const TileDesc* tiles;         // assign-step tiles, n_tiles entries
   const BlockConst* bconst;      // per-camera block constants
+  const float4* pray;            // separable pair rays (PairDev::ga, gb)
   int n_tiles;
 };
 
@@ -61,7 +61,7 @@ struct OutDev {
   uint32_t* rep;
   unsigned long long* key;
   long long max_cells;
-  double s0_m;                   // coarse edge, metres
+  float s0_m;                    // coarse edge, metres
   double unit_m;                 // metres per depth unit
 };
 
@@ -72,14 +72,14 @@ struct Geometry {
   int count_chunks;              // 1024-pixel chunks per block of the coarse-count step
   int tiles_max;                 // 32x16 tiles per camera (max over cams)
   int emit_blocks;
+  TileIndex tiles;               // assign-step tiles
 };
 
 cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cudaStream_t s);
 
-// Host-side construction of the assign step's tile list and per-camera block constants
-// from the rig constants (caller-sized arrays: n_tiles_for(rig) and rig.n_cams entries).
-int n_tiles_for(const RigDev& rig);
-void fill_tiles(const RigDev& rig, TileDesc* out);
+// Host-side construction of the assign step's tile index and per-camera block constants
+// (caller-sized array of rig.n_cams entries) from the rig constants.
+int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);
 // ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp,

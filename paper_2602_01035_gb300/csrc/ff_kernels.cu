@@ -9,8 +9,8 @@
 //            hash insertion; (d) per (tile, cell): member count, representative
 //            (Sec. II.5(2)a), smallest weight exponent and exact fixed-point sums of
 //            omega, omega P, omega RGB (Eq. 11), written as one partial record
-//   link     per partial: push it onto its cell's list (cells own dense slots: coarse
-//            cell c owns 8^level(c) consecutive slots, sized by the count step's last block)
+//            and pushed onto its cell's list (cells own dense slots: coarse cell c owns
+//            8^level(c) consecutive slots, sized by the count step's last block)
 //   reduce   per cell: walk its partials, combine them, stage the fused cell, mark its
 //            representative; the used hash slots are cleared for the next frame
 //   scan     ranks of the representatives (output order) and frame statistics, one kernel
@@ -29,7 +29,7 @@ namespace ffl {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCountPx = 4;                       // pixels per thread in the count step
+constexpr int kCountPx = 8;                       // pixels per thread in the count step
 constexpr int kCountBlockPx = kThreads * kCountPx;
 constexpr int kTileW = 32, kTileH = 16;           // assign/accum tile: 8 warps x 2 rows
 constexpr int kTilePx = kTileW * kTileH;
@@ -42,17 +42,14 @@ constexpr float kInvLn2 = 1.44269504088896340736f;
 __device__ __forceinline__ unsigned coarse_insert(const Tables& t, unsigned long long key) {
   unsigned h = (unsigned)mix64(key) & t.cmask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    unsigned long long cur = __ldcg(&t.coarse[h].key);
-    if (cur == key) return h;
+    // one round trip per probe: the swap either claims an empty slot or reports its key
+    const unsigned long long cur = atomicCAS(&t.coarse[h].key, kKeyEmpty, key);
     if (cur == kKeyEmpty) {
-      cur = atomicCAS(&t.coarse[h].key, kKeyEmpty, key);
-      if (cur == kKeyEmpty) {
-        const unsigned n = atomicAdd(&t.cnt->n_coarse, 1u);
-        if (n <= t.cmask) t.cused[n] = h;
-        return h;
-      }
-      if (cur == key) return h;
+      const unsigned n = atomicAdd(&t.cnt->n_coarse, 1u);
+      if (n <= t.cmask) t.cused[n] = h;
+      return h;
     }
+    if (cur == key) return h;
     h = (h + 1) & t.cmask;
   }
   atomicOr(&t.cnt->error, kErrCoarseFull);
@@ -73,59 +70,37 @@ __device__ __forceinline__ unsigned coarse_lvbase(const Tables& t, unsigned long
   return kBaseNone;
 }
 
-template <int NT, typename T>
-__device__ __forceinline__ T block_excl_scan(T v, T* s_w, T& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    T w = lane < NT / 32 ? s_w[lane] : (T)0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < NT / 32) s_w[lane] = w;
-  }
-  __syncthreads();
-  total = s_w[NT / 32 - 1];
-  const T before = warp ? s_w[warp - 1] : (T)0;
-  __syncthreads();
-  return before + x - v;
-}
-
-// Sec. II.5(1)d for every coarse cell once all counts are in: level l and the first of
-// its 8^l dense cell slots (exclusive prefix over the coarse cells in claim order).
-__device__ void assign_levels(Tables& t) {
-  __shared__ unsigned long long s_w[kThreads / 32];
-  const unsigned n_coarse = min(__ldcg(&t.cnt->n_coarse), t.cmask + 1u);
-  unsigned long long carry = 0;
-  for (unsigned base = 0; base < n_coarse; base += kThreads) {
+// Sec. II.5(1)d for every coarse cell once all counts are in: its level l and a range of
+// 8^l dense cell slots.  Ranges are claimed with one atomic per warp (an inclusive scan of
+// the sizes inside the warp), so their placement depends on scheduling; no result does.
+__global__ void __launch_bounds__(kThreads) k_levels(Tables t) {
+  const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long cap = t.max_slots;
+  for (unsigned base = blockIdx.x * blockDim.x; base < n_coarse; base += gridDim.x * blockDim.x) {
     const unsigned i = base + threadIdx.x;
     unsigned cs = 0, l = 0;
     unsigned long long size = 0;
     if (i < n_coarse) {
-      cs = __ldcg(&t.cused[i]);
-      l = (unsigned)level_for(__ldcg(&t.coarse[cs].count), t.n_min, t.max_level);
-      size = 1ull << (3 * l);                  // 8^l <= 2^42
+      cs = t.cused[i];
+      l = (unsigned)level_for(t.coarse[cs].count, t.n_min, t.max_level);
+      size = min(1ull << (3 * l), cap + 1ull);           // 8^l, clamped: never fits then
     }
-    unsigned long long total;
-    const unsigned long long ex = block_excl_scan<kThreads, unsigned long long>(size, s_w, total);
+    unsigned long long x = size;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    unsigned long long wbase = 0;
+    if (lane == 31 && x) wbase = atomicAdd(&t.cnt->n_slots, x);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
     if (i < n_coarse) {
-      const unsigned long long b = carry + ex;
-      t.coarse[cs].lvbase = (l << 27) | (b + size <= t.max_slots ? (unsigned)b : kBaseNone);
+      const unsigned long long b = wbase + x - size;
+      const bool fits = b + size <= cap;
+      t.coarse[cs].lvbase = (l << 27) | (fits ? (unsigned)b : kBaseNone);
+      if (!fits) atomicOr(&t.cnt->error, kErrSlots);
     }
-    carry += total;
-  }
-  if (threadIdx.x == 0) {
-    t.cnt->n_slots = (unsigned)min(carry, (unsigned long long)t.max_slots);
-    if (carry > t.max_slots) atomicOr(&t.cnt->error, kErrSlots);
   }
 }
 
@@ -172,140 +147,160 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 }
 
 // Sum over the K-1 neighbour views of d_ij^2 (Eq. 6) in depth units^2, as ff (sh, sl).
+// Pixel (x, y) of the block's camera at z-depth z; the transform into view j (Eq. 4) uses
+// the separable pair rays, so that a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff
+// product and one ff sum per component.  Views go in groups of kViewGroup: every view of
+// a group is projected and its depth gather issued before any residual is formed, so the
+// gathers of a group overlap instead of following one another.
+constexpr int kViewGroup = 3;
+
 template <typename DT>
-__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1,
+__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const float4* __restrict__ pray,
                                              const float2* __restrict__ rays,
-                                             const FramePtrs& fp, float z, float2 rx, float2 ry,
+                                             const FramePtrs& fp, float z, int x, int y,
                                              float& sh, float& sl, int& nview) {
-  float pxh, pxl, pyh, pyl;
-  two_prod(z, rx.x, pxh, pxl);
-  pxl = __fmaf_rn(z, rx.y, pxl);
-  two_prod(z, ry.x, pyh, pyl);
-  pyl = __fmaf_rn(z, ry.y, pyl);
   sh = 0.0f;
   sl = 0.0f;
   nview = 0;
-  for (int q = 0; q < k1; ++q) {
-    const PairDev& P = bc.pair[q];
-    const CamDev& J = bc.nb[q];
-    float a[3];
+  for (int q0 = 0; q0 < k1; q0 += kViewGroup) {
+    float ah[kViewGroup][3], al[kViewGroup][3];
+    int px[kViewGroup], py[kViewGroup];
+    DT Dj[kViewGroup];
+    bool ok[kViewGroup];
+    // Eq. 4: transform, projection, nearest pixel and field-of-view test of each view
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      a[k] = __fmaf_rn(P.Rh[3 * k], pxh, __fmaf_rn(P.Rh[3 * k + 1], pyh,
-                                                   __fmaf_rn(P.Rh[3 * k + 2], z, P.th[k])));
-    float ah[3], al[3];
-    bool have = false;
-    if (a[2] < kZGuard) {       // close to camera j's image plane: decide the sign exactly
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        ff_affine_row(P.Rh + 3 * k, P.Rl + 3 * k, P.th[k], P.tl[k], pxh, pxl, pyh, pyl, z,
-                      ah[k], al[k]);
-      have = true;
-      if (!(ah[2] > 0.0f)) continue;                    // behind camera j (Eq. 4 FoV check)
-      a[0] = ah[0];
-      a[1] = ah[1];
-      a[2] = ah[2];
+    for (int g = 0; g < kViewGroup; ++g) {
+      ok[g] = false;
+      px[g] = 0;
+      py[g] = 0;
+      Dj[g] = (DT)0;
+      const int q = q0 + g;
+      if (q >= k1) continue;
+      const PairDev& P = bc.pair[q];
+      const CamDev& J = bc.nb[q];
+      const float4 a01 = __ldg(pray + P.ga + 2 * x), a2 = __ldg(pray + P.ga + 2 * x + 1);
+      const float4 b01 = __ldg(pray + P.gb + 2 * y), b2 = __ldg(pray + P.gb + 2 * y + 1);
+      ff_ray_affine(a01.x, a01.y, b01.x, b01.y, z, P.th[0], P.tl[0], ah[g][0], al[g][0]);
+      ff_ray_affine(a01.z, a01.w, b01.z, b01.w, z, P.th[1], P.tl[1], ah[g][1], al[g][1]);
+      ff_ray_affine(a2.x, a2.y, b2.x, b2.y, z, P.th[2], P.tl[2], ah[g][2], al[g][2]);
+      fast_two_sum(ah[g][2], al[g][2], ah[g][2], al[g][2]);   // sign of a_z is that of ah
+      if (!(ah[g][2] > 0.0f)) continue;                        // behind camera j
+      // float32 estimate of u + 1/2 from the ff high parts (relative error ~1e-7, so a
+      // few 1e-4 px); within kTieBandPx of a tie the pixel is decided exactly
+      const float fu = __fadd_rn(__fmaf_rn(J.fx, __fdividef(ah[g][0], ah[g][2]), J.cx), 0.5f);
+      const float fv = __fadd_rn(__fmaf_rn(J.fy, __fdividef(ah[g][1], ah[g][2]), J.cy), 0.5f);
+      if (!(fu > -1.0f && fu < (float)J.W + 1.0f && fv > -1.0f && fv < (float)J.H + 1.0f))
+        continue;
+      const float ru = rintf(fu), rv = rintf(fv);
+      px[g] = fabsf(fu - ru) < kTieBandPx
+                  ? exact_round(J.fxh, J.fxl, J.cxh, J.cxl, ah[g][0], al[g][0], ah[g][2], al[g][2], ru)
+                  : (int)floorf(fu);
+      py[g] = fabsf(fv - rv) < kTieBandPx
+                  ? exact_round(J.fyh, J.fyl, J.cyh, J.cyl, ah[g][1], al[g][1], ah[g][2], al[g][2], rv)
+                  : (int)floorf(fv);
+      if (px[g] < 0 || px[g] >= J.W || py[g] < 0 || py[g] >= J.H) continue;
+      Dj[g] = __ldg(static_cast<const DT*>(fp.depth[P.j]) + (long long)py[g] * J.W + px[g]);
+      ok[g] = true;
     }
-    // float32 estimate of u + 1/2 (error well below kTieBandPx; near ties the pixel is
-    // decided exactly below)
-    const float fu = __fadd_rn(__fmaf_rn(J.fx, __fdividef(a[0], a[2]), J.cx), 0.5f);
-    const float fv = __fadd_rn(__fmaf_rn(J.fy, __fdividef(a[1], a[2]), J.cy), 0.5f);
-    if (!(fu > -1.0f && fu < (float)J.W + 1.0f && fv > -1.0f && fv < (float)J.H + 1.0f))
-      continue;
-    const float ru = rintf(fu), rv = rintf(fv);
-    const bool tie_u = fabsf(fu - ru) < kTieBandPx, tie_v = fabsf(fv - rv) < kTieBandPx;
-    if ((tie_u || tie_v) && !have) {
+    // Eq. 5-6 for the views whose gathered depth is valid
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        ff_affine_row(P.Rh + 3 * k, P.Rl + 3 * k, P.th[k], P.tl[k], pxh, pxl, pyh, pyl, z,
-                      ah[k], al[k]);
-      have = true;
-    }
-    const int px = tie_u ? exact_round(J.fxh, J.fxl, J.cxh, J.cxl, ah[0], al[0], ah[2], al[2], ru)
-                         : (int)floorf(fu);
-    const int py = tie_v ? exact_round(J.fyh, J.fyl, J.cyh, J.cyl, ah[1], al[1], ah[2], al[2], rv)
-                         : (int)floorf(fv);
-    if (px < 0 || px >= J.W || py < 0 || py >= J.H) continue;   // field-of-view check
-    const DT Dj = __ldg(static_cast<const DT*>(fp.depth[P.j]) + (long long)py * J.W + px);
-    if (!Depth<DT>::valid(Dj)) continue;
-    if (!have) {
+    for (int g = 0; g < kViewGroup; ++g) {
+      if (!ok[g] || !Depth<DT>::valid(Dj[g])) continue;
+      const CamDev& J = bc.nb[q0 + g];
+      // Q = D_j(u_j) (rx_j, ry_j, 1) in camera-j coordinates (rigid motion keeps d)
+      const float zj = Depth<DT>::z(Dj[g]);
+      const float2 qx = __ldg(rays + J.ray_x + px[g]), qy = __ldg(rays + J.ray_y + py[g]);
+      float qh[3], ql[3];
+      two_prod(zj, qx.x, qh[0], ql[0]);
+      ql[0] = __fmaf_rn(zj, qx.y, ql[0]);
+      two_prod(zj, qy.x, qh[1], ql[1]);
+      ql[1] = __fmaf_rn(zj, qy.y, ql[1]);
+      qh[2] = zj;
+      ql[2] = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        ff_affine_row(P.Rh + 3 * k, P.Rl + 3 * k, P.th[k], P.tl[k], pxh, pxl, pyh, pyl, z,
-                      ah[k], al[k]);
+      for (int k = 0; k < 3; ++k) {                    // d^2 = |a - Q|^2 in ff
+        float s, e, p, pe, tt;
+        two_sum(ah[g][k], -qh[k], s, e);
+        e = __fadd_rn(e, __fsub_rn(al[g][k], ql[k]));
+        // (s + e)^2 = s^2 + 2 s e + e^2; e^2 is below the ff rounding of the sum
+        two_prod(s, s, p, pe);
+        pe = __fmaf_rn(__fmul_rn(2.0f, s), e, pe);
+        two_sum(sh, p, sh, tt);
+        sl = __fadd_rn(sl, __fadd_rn(tt, pe));
+      }
+      ++nview;
     }
-    // Eq. 5: Q = D_j(u_j) (rx_j, ry_j, 1) in camera-j coordinates (rigid motion keeps d).
-    const float zj = Depth<DT>::z(Dj);
-    const float2 qx = __ldg(rays + J.ray_x + px), qy = __ldg(rays + J.ray_y + py);
-    float qh[3], ql[3];
-    two_prod(zj, qx.x, qh[0], ql[0]);
-    ql[0] = __fmaf_rn(zj, qx.y, ql[0]);
-    two_prod(zj, qy.x, qh[1], ql[1]);
-    ql[1] = __fmaf_rn(zj, qy.y, ql[1]);
-    qh[2] = zj;
-    ql[2] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {                      // Eq. 6: d^2 = |a - Q|^2 in ff
-      float s, e, dh, dl, p, pe, t;
-      two_sum(ah[k], -qh[k], s, e);
-      e = __fadd_rn(e, __fsub_rn(al[k], ql[k]));
-      fast_two_sum(s, e, dh, dl);
-      two_prod(dh, dh, p, pe);
-      pe = __fmaf_rn(__fmul_rn(2.0f, dh), dl, pe);
-      two_sum(sh, p, sh, t);
-      sl = __fadd_rn(sl, __fadd_rn(t, pe));
-    }
-    ++nview;
   }
 }
 
 // ------------------------------------------------------------------ count step
 template <typename DT>
-__device__ __forceinline__ void load4(const DT* __restrict__ d, const float* __restrict__ c,
-                                      long long p0, long long npx, DT dv[4], float cv[4]) {
-  const bool full = p0 + 3 < npx;
+__device__ __forceinline__ void load8(const DT* __restrict__ d, const float* __restrict__ c,
+                                      long long p0, long long npx, DT dv[8], float cv[8]) {
+  const bool full = p0 + 7 < npx;
   if constexpr (sizeof(DT) == 2) {
-    if (full && ((reinterpret_cast<uintptr_t>(d + p0) & 7) == 0)) {
-      const uint2 u = __ldcs(reinterpret_cast<const uint2*>(d + p0));
-      dv[0] = (DT)(u.x & 0xffff); dv[1] = (DT)(u.x >> 16);
-      dv[2] = (DT)(u.y & 0xffff); dv[3] = (DT)(u.y >> 16);
+    if (full && ((reinterpret_cast<uintptr_t>(d + p0) & 15) == 0)) {
+      const uint4 u = __ldcs(reinterpret_cast<const uint4*>(d + p0));
+      const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { dv[2 * k] = (DT)(w[k] & 0xffff); dv[2 * k + 1] = (DT)(w[k] >> 16); }
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dv[k] = (p0 + k < npx) ? d[p0 + k] : (DT)0;
+      for (int k = 0; k < 8; ++k) dv[k] = (p0 + k < npx) ? d[p0 + k] : (DT)0;
     }
   } else {
     if (full && ((reinterpret_cast<uintptr_t>(d + p0) & 15) == 0)) {
-      const float4 f = __ldcs(reinterpret_cast<const float4*>(d + p0));
-      dv[0] = f.x; dv[1] = f.y; dv[2] = f.z; dv[3] = f.w;
+      const float4 f0 = __ldcs(reinterpret_cast<const float4*>(d + p0));
+      const float4 f1 = __ldcs(reinterpret_cast<const float4*>(d + p0) + 1);
+      dv[0] = f0.x; dv[1] = f0.y; dv[2] = f0.z; dv[3] = f0.w;
+      dv[4] = f1.x; dv[5] = f1.y; dv[6] = f1.z; dv[7] = f1.w;
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dv[k] = (p0 + k < npx) ? d[p0 + k] : (DT)0;
+      for (int k = 0; k < 8; ++k) dv[k] = (p0 + k < npx) ? d[p0 + k] : (DT)0;
     }
   }
   if (full && ((reinterpret_cast<uintptr_t>(c + p0) & 15) == 0)) {
-    const float4 f = __ldcs(reinterpret_cast<const float4*>(c + p0));
-    cv[0] = f.x; cv[1] = f.y; cv[2] = f.z; cv[3] = f.w;
+    const float4 f0 = __ldcs(reinterpret_cast<const float4*>(c + p0));
+    const float4 f1 = __ldcs(reinterpret_cast<const float4*>(c + p0) + 1);
+    cv[0] = f0.x; cv[1] = f0.y; cv[2] = f0.z; cv[3] = f0.w;
+    cv[4] = f1.x; cv[5] = f1.y; cv[6] = f1.z; cv[7] = f1.w;
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cv[k] = (p0 + k < npx) ? c[p0 + k] : 0.0f;
+    for (int k = 0; k < 8; ++k) cv[k] = (p0 + k < npx) ? c[p0 + k] : 0.0f;
+  }
+}
+
+// Adds n points to coarse key k: the block table first, the global table after 64 probes.
+template <int TS>
+__device__ __forceinline__ void count_add(const Tables& t, unsigned long long* s_key,
+                                          unsigned* s_cnt, unsigned long long k, unsigned n) {
+  const int h = local_pos<TS>(s_key, kKeyEmpty, k, 64);
+  if (h >= 0) {
+    atomicAdd(&s_cnt[h], n);
+  } else {
+    const unsigned slot = coarse_insert(t, k);
+    if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, n);
   }
 }
 
 template <typename DT>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
         int blocks_x, int chunks) {
-  constexpr int TS = 2 * kCountBlockPx;
+  constexpr int TS = 2048;                                      // block table of coarse keys
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
   __shared__ unsigned s_red[kThreads / 32][9];
   const RigDev& rig = *rigp;
   const int cam = blockIdx.y;
-  const CamDev& C = rig.cam[cam];
+  // the camera's constants and the rig's scalars in registers (they would otherwise be
+  // re-read for every pixel, as the atomics below may alias memory for the compiler)
+  const CamDev C = rig.cam[cam];
+  const float tau = rig.tau, inv_s0u = rig.inv_s0u;
+  const int use_conf = rig.use_conf, lim = kKeyBias >> rig.max_level;
   const long long npx = (long long)C.W * C.H;
   const int bid = cam * blocks_x + blockIdx.x;
-  __shared__ bool s_last;
-  const long long c0 = (long long)blockIdx.x * chunks;          // first 1024-pixel chunk
+  const long long c0 = (long long)blockIdx.x * chunks;          // first chunk of 2048 pixels
   const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
   __syncthreads();
@@ -314,67 +309,108 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   const float* __restrict__ cf = fp.conf[cam];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned nv = 0, ng = 0, noor = 0;
-  unsigned bmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, bmax[3] = {0u, 0u, 0u};
-  DT dv[4];
-  float cv[4];
+  float fmn[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+  float fmx[3] = {__int_as_float(0xff800000), __int_as_float(0xff800000), __int_as_float(0xff800000)};
+  DT dv[kCountPx];
+  float cv[kCountPx];
   long long pn = (c0 * kThreads + threadIdx.x) * kCountPx;
-  if (!idle && pn < npx) load4<DT>(dep, cf, pn, npx, dv, cv);
+  if (!idle && pn < npx) load8<DT>(dep, cf, pn, npx, dv, cv);
+  int y = (int)((unsigned)pn / (unsigned)C.W);                  // W H <= 2^30
+  int x = (int)((unsigned)pn - (unsigned)y * (unsigned)C.W);
   for (int ch = 0; ch < (idle ? 0 : chunks); ++ch) {
     const long long pc = pn;
     if ((c0 + ch) * kCountBlockPx >= npx) break;                 // uniform over the block
-    DT dcur[4];
-    float ccur[4];
+    DT dcur[kCountPx];
+    float ccur[kCountPx];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { dcur[k] = dv[k]; ccur[k] = cv[k]; }
+    for (int k = 0; k < kCountPx; ++k) { dcur[k] = dv[k]; ccur[k] = cv[k]; }
     pn = pc + kCountBlockPx;                                      // prefetch the next chunk
-    if (ch + 1 < chunks && pn < npx) load4<DT>(dep, cf, pn, npx, dv, cv);
-    if (pc >= npx) continue;
-    unsigned long long rk[kCountPx] = {kKeyEmpty, kKeyEmpty, kKeyEmpty, kKeyEmpty};
-    unsigned rn[kCountPx] = {1u, 1u, 1u, 1u};
-    int y = (int)((unsigned)pc / (unsigned)C.W);                  // W H <= 2^30
-    int x = (int)((unsigned)pc - (unsigned)y * (unsigned)C.W);
+    if (ch + 1 < chunks && pn < npx) load8<DT>(dep, cf, pn, npx, dv, cv);
+    // Sec. II.5(1)c density estimate. Runs of equal coarse cells along the thread's
+    // pixels: the first run (if the thread has several) and the last run are kept, the
+    // ones between go to the block table at once (rare: a cell spans ~70 pixels here).
+    unsigned long long khead = kKeyEmpty, ktail = kKeyEmpty;
+    unsigned nhead = 0u, run = 0u, nruns = 0u;
+    int cx = 0, cy = 0, cz = 0;
+    if (pc < npx) {
+      int xx = x, yy = y;
+      float ry = __ldg(&rays[C.ray_y + min(yy, C.H - 1)].x);
 #pragma unroll
-    for (int k = 0; k < kCountPx; ++k) {
-      if (pc + k < npx && Depth<DT>::valid(dcur[k])) {
-        ++nv;
-        if (!rig.use_conf || ccur[k] > rig.tau) {                 // Eq. 9
-          ++ng;
-          float P[3], r[3];
-          world_point(C, Depth<DT>::z(dcur[k]), __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
+      for (int k = 0; k < kCountPx; ++k) {
+        if (pc + k < npx && Depth<DT>::valid(dcur[k])) {
+          ++nv;
+          if (!use_conf || ccur[k] > tau) {                       // Eq. 9
+            ++ng;
+            float P[3];
+            world_point(C, Depth<DT>::z(dcur[k]), __ldg(&rays[C.ray_x + xx].x), ry, P);
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const unsigned o = ordered(P[a]);
-            bmin[a] = min(bmin[a], o);
-            bmax[a] = max(bmax[a], o);
+            for (int a = 0; a < 3; ++a) { fmn[a] = fminf(fmn[a], P[a]); fmx[a] = fmaxf(fmx[a], P[a]); }
+            // coarse coordinates floor(P / s0); the finest index floor(r 2^Lmax) is in
+            // [-2^19, 2^19) exactly when floor(r) is in [-2^(19-Lmax), 2^(19-Lmax))
+            const int ix = (int)floorf(__fmul_rn(P[0], inv_s0u));
+            const int iy = (int)floorf(__fmul_rn(P[1], inv_s0u));
+            const int iz = (int)floorf(__fmul_rn(P[2], inv_s0u));
+            if (ix >= -lim && ix < lim && iy >= -lim && iy < lim && iz >= -lim && iz < lim) {
+              if (run && ix == cx && iy == cy && iz == cz) {
+                ++run;
+              } else {
+                if (run) {                                        // a run ends
+                  if (nruns == 1u) {
+                    khead = pack_key(0, cx, cy, cz);
+                    nhead = run;
+                  } else {
+                    count_add<TS>(t, s_key, s_cnt, pack_key(0, cx, cy, cz), run);
+                  }
+                }
+                cx = ix; cy = iy; cz = iz;
+                run = 1u;
+                ++nruns;
+              }
+            } else {
+              ++noor;
+            }
           }
-          if (grid_coords(rig, P, r)) rk[k] = coarse_key(r);
-          else ++noor;
+        }
+        if (++xx == C.W) {
+          xx = 0;
+          ++yy;
+          ry = __ldg(&rays[C.ray_y + min(yy, C.H - 1)].x);
         }
       }
-      if (++x == C.W) { x = 0; ++y; }
     }
-    // Sec. II.5(1)c density estimate: merge the thread's equal neighbours, then one
-    // shared-memory update per distinct key (global if the block table is full)
+    {
+      if (run) ktail = pack_key(0, cx, cy, cz);
+      // merge the lanes' runs along the warp (consecutive lanes hold consecutive pixels):
+      // a lane's first run continues the previous lane's last run when the keys agree
+      const unsigned long long kfirst = nruns >= 2u ? khead : ktail;
+      const unsigned long long kprev = __shfl_up_sync(0xffffffffu, ktail, 1);
+      const bool cont = lane > 0 && ktail != kKeyEmpty && kfirst == kprev;
+      // a continuing head run is credited to the previous lane's chain
+      const unsigned give = (cont && nruns >= 2u) ? nhead : 0u;
+      unsigned v = run + __shfl_down_sync(0xffffffffu, give, 1) * (lane < 31 ? 1u : 0u);
+      bool start = !(cont && nruns == 1u);
+      const bool nstart = __shfl_down_sync(0xffffffffu, (unsigned)start, 1) != 0u;
 #pragma unroll
-    for (int k = 1; k < kCountPx; ++k)
-      if (rk[k] != kKeyEmpty && rk[k] == rk[k - 1]) {
-        rn[k] += rn[k - 1];
-        rk[k - 1] = kKeyEmpty;
+      for (int d = 1; d < 32; d <<= 1) {                          // segmented inclusive scan
+        const unsigned v2 = __shfl_up_sync(0xffffffffu, v, d);
+        const bool f2 = __shfl_up_sync(0xffffffffu, (unsigned)start, d) != 0u;
+        if (lane >= d) {
+          if (!start) v += v2;
+          start = start || f2;
+        }
       }
-#pragma unroll
-    for (int j = 0; j < kCountPx; ++j) {
-      if (rk[j] == kKeyEmpty) continue;
-      const int h = local_pos<TS>(s_key, kKeyEmpty, rk[j], 64);
-      if (h >= 0) {
-        atomicAdd(&s_cnt[h], rn[j]);
-      } else {
-        const unsigned slot = coarse_insert(t, rk[j]);
-        if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, rn[j]);
-      }
+      if (nruns >= 2u && !cont) count_add<TS>(t, s_key, s_cnt, khead, nhead);
+      if (ktail != kKeyEmpty && (lane == 31 || nstart)) count_add<TS>(t, s_key, s_cnt, ktail, v);
     }
+    x += kCountBlockPx;                                           // next chunk's first pixel
+    while (x >= C.W) { x -= C.W; ++y; }
   }
   // per-block pixel counts and extent
-  unsigned vals[9] = {nv, ng, noor, bmin[0], bmin[1], bmin[2], bmax[0], bmax[1], bmax[2]};
+  unsigned vals[9] = {nv, ng, noor, ordered(fmn[0]), ordered(fmn[1]), ordered(fmn[2]),
+                      ordered(fmx[0]), ordered(fmx[1]), ordered(fmx[2])};
+  if (ng == 0) {
+    for (int a = 0; a < 3; ++a) { vals[3 + a] = 0xffffffffu; vals[6 + a] = 0u; }
+  }
   vals[0] = __reduce_add_sync(0xffffffffu, vals[0]);
   vals[1] = __reduce_add_sync(0xffffffffu, vals[1]);
   vals[2] = __reduce_add_sync(0xffffffffu, vals[2]);
@@ -408,16 +444,6 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     const unsigned slot = coarse_insert(t, key);
     if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, s_cnt[i]);
   }
-  // the last block to finish (fenced counter, no waiting) sizes the cells' slot ranges
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0)
-    s_last = atomicAdd(&t.cnt->count_done, 1u) == gridDim.x * gridDim.y - 1;
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    assign_levels(t);
-  }
 }
 
 // ------------------------------------------------------------------ assign step
@@ -441,6 +467,15 @@ constexpr size_t kSmRGB = align16(kSmC + 4 * kTilePx);             // u32[tile] 
 constexpr size_t kAssignSmem = align16(kSmRGB + 4 * kTilePx);
 constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
 
+// rint(v) for 0 <= v < 2^37 as hi 2^22 + lo with lo in [0, 2^22], using 32-bit conversions
+// only: v - floor(v 2^-22) 2^22 is exact (both are multiples of ulp(v)), and adding the even
+// integer hi 2^22 does not change a round-half-even decision.
+__device__ __forceinline__ void split_round(float v, unsigned& lo, unsigned& hi) {
+  const float hf = floorf(__fmul_rn(v, 1.0f / (float)(1u << kLoBits)));
+  hi = (unsigned)hf;
+  lo = __float2uint_rn(__fmaf_rn(-hf, (float)(1u << kLoBits), v));
+}
+
 // First probe of a point's coarse record (read-only during the assign step, L1-cached);
 // coarse_lvbase() finishes the probe once the value is needed.
 __device__ __forceinline__ ulonglong2 coarse_probe(const Tables& t, unsigned long long key, unsigned& h) {
@@ -451,7 +486,7 @@ __device__ __forceinline__ ulonglong2 coarse_probe(const Tables& t, unsigned lon
 template <typename DT>
 __global__ void __launch_bounds__(kThreads, 3)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
-         TraceDev tr, float unit_m) {
+         TraceDev tr, float unit_m, TileIndex ti) {
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
   unsigned* s_fk = reinterpret_cast<unsigned*>(smem + kSmFK);
@@ -470,8 +505,20 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   __shared__ unsigned s_n, s_base, s_ng;
 
   const RigDev& rig = *rigp;
-  const TileDesc td = t.tiles[blockIdx.x];
-  const int cam = td.cam, W = td.W, H = td.H, k1 = td.k1;
+  // this block's tile: binary search of the per-camera tile ranges (constant bank)
+  int cam = 0;
+  for (int lo = 0, hi = ti.n_cams - 1; lo <= hi;) {
+    const int mid = (lo + hi) >> 1;
+    if (ti.first[mid] <= (int)blockIdx.x) { cam = mid; lo = mid + 1; } else { hi = mid - 1; }
+  }
+  const int W = ti.W[cam], H = ti.H[cam], k1 = ti.k1;
+  struct { int x0, y0; long long off; } td;
+  {
+    const int local = (int)blockIdx.x - ti.first[cam], tiles_x = (W + kTileW - 1) / kTileW;
+    td.x0 = (local % tiles_x) * kTileW;
+    td.y0 = (local / tiles_x) * kTileH;
+    td.off = ti.off[cam];
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
@@ -557,9 +604,9 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     gi[j] = td.off + (long long)y * W + x;
     const float z = s_z[i];
     const float c = s_c[i];
-    const float2 rx = __ldg(rays + C.ray_x + x), ry = __ldg(rays + C.ray_y + y);
+    const float rx = __ldg(&rays[C.ray_x + x].x), ry = __ldg(&rays[C.ray_y + y].x);
     float P[3], r[3];
-    world_point(C, z, rx.x, ry.x, P);                                 // Eq. 8
+    world_point(C, z, rx, ry, P);                                     // Eq. 8
     has[j] = grid_coords(rig, P, r);
     // start the lookup of the coarse cell's level and slot range (Sec. II.5(1)d)
     const unsigned long long ck = has[j] ? coarse_key(r) : kKeyEmpty;
@@ -569,7 +616,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     float sh = 0.0f, sl = 0.0f, eh = 0.0f, el = 0.0f;
     int nview = 0;
     if (rig.use_cons && k1 > 0) {
-      residual_sum<DT>(bc, k1, rays, fp, z, rx, ry, sh, sl, nview);
+      residual_sum<DT>(bc, k1, t.pray, rays, fp, z, x, y, sh, sl, nview);
       fast_two_sum(sh, sl, sh, sl);
       two_prod(sh, rig.einv_h, eh, el);                               // Eq. 7 exponent
       el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
@@ -667,17 +714,19 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     const int sh = mexp[j] - s_min[e];
     const float w = sh > 62 ? 0.0f : __fmul_rn(mu[j], pow2f(kFixShift - sh));
     const unsigned rgb = s_rgb[threadIdx.x + j * kThreads];
-    unsigned long long q[7];
-    q[0] = __float2ull_rn(w);
+    float v[7];
+    v[0] = w;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) q[1 + a] = __float2ull_rn(__fmul_rn(w, frac[j][a]));
+    for (int a = 0; a < 3; ++a) v[1 + a] = __fmul_rn(w, frac[j][a]);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      q[4 + a] = __float2ull_rn(__fmul_rn(w, (float)((rgb >> (8 * a)) & 0xffu) * 0.00390625f));
+      v[4 + a] = __fmul_rn(w, (float)((rgb >> (8 * a)) & 0xffu) * 0.00390625f);
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
-      atomicAdd(&s_acc[(2 * a) * kAssignNL + e], (unsigned)(q[a] & ((1ull << kLoBits) - 1ull)));
-      atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], (unsigned)(q[a] >> kLoBits));
+      unsigned lo, hi;
+      split_round(v[a], lo, hi);
+      atomicAdd(&s_acc[(2 * a) * kAssignNL + e], lo);
+      atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], hi);
     }
   }
   if (threadIdx.x == 0) s_base = base_pi;
@@ -698,28 +747,23 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
                s_acc[(2 * a) * kAssignNL + e];
     t.part[pi] = p;
-  }
-}
-
-// ------------------------------------------------------------------ link step
-// Pushes every partial onto its cell's list and records the cell's smallest exponent; the
-// first partial of a cell also claims the cell for the reduce step.
-__global__ void __launch_bounds__(kThreads) k_link(Tables t) {
-  const unsigned np = min(t.cnt->n_partials, t.max_partials);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-    const unsigned slot = t.part[i].slot;
-    const int mm = t.part[i].mmin;
-    atomicMin(&t.fmmin[slot], mm);
-    const unsigned prev = atomicExch(&t.fhead[slot], i);
-    t.pnext[i] = prev;
+    // file the partial under its cell: list push, smallest exponent, first-claim of the cell
+    atomicMin(&t.fmmin[p.slot], p.mmin);
+    const unsigned prev = atomicExch(&t.fhead[p.slot], pi);
+    t.pnext[pi] = prev;
     if (prev == kSlotNone) {
       const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
-      if (n < t.max_slots) t.fused[n] = slot;
+      if (n < t.max_slots) t.fused[n] = p.slot;
     }
   }
 }
 
 // ------------------------------------------------------------------ reduce step
+// u64 -> float32 through two 32-bit conversions (at most two roundings)
+__device__ __forceinline__ float u64_to_f32(unsigned long long x) {
+  return __fmaf_rn(__uint2float_rn((unsigned)(x >> 32)), 4294967296.0f, __uint2float_rn((unsigned)x));
+}
+
 __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
   const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
@@ -746,20 +790,19 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
       if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
       const unsigned g = head != kSlotNone ? ~(unsigned)(rep & 0xffffffffull) : 0xffffffffu;
       CellOut c;
+      // Eq. 11 in float32: position = edge (k + S_k / S_0), colour = 256 S_c / S_0,
+      // weight = S_0 2^-(36 + mmin); each result is within a few float32 roundings
       const int l = (int)(key >> 60);
-      const double edge = ldexp(out.s0_m, -l);
-      const double kx = (double)((int)((key >> 40) & 0xfffff) - kKeyBias);
-      const double ky = (double)((int)((key >> 20) & 0xfffff) - kKeyBias);
-      const double kz = (double)((int)(key & 0xfffff) - kKeyBias);
-      const double Wq = (double)S[0];
-      const double inv = S[0] ? 1.0 / Wq : __longlong_as_double(0x7ff8000000000000ll);
-      c.pos[0] = (float)(edge * (kx + (double)S[1] * inv));
-      c.pos[1] = (float)(edge * (ky + (double)S[2] * inv));
-      c.pos[2] = (float)(edge * (kz + (double)S[3] * inv));
-      c.rgb[0] = (float)(256.0 * (double)S[4] * inv);
-      c.rgb[1] = (float)(256.0 * (double)S[5] * inv);
-      c.rgb[2] = (float)(256.0 * (double)S[6] * inv);
-      c.weight = (float)ldexp(Wq, -kFixShift - mmin);
+      const float edge = __fmul_rn(out.s0_m, pow2f(-l));
+      const float Wf = u64_to_f32(S[0]);
+      const float inv = S[0] ? __frcp_rn(Wf) : __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ka = (int)((key >> (40 - 20 * a)) & 0xfffff) - kKeyBias;
+        c.pos[a] = __fmaf_rn(edge, (float)ka, __fmul_rn(edge, __fmul_rn(u64_to_f32(S[1 + a]), inv)));
+        c.rgb[a] = __fmul_rn(256.0f, __fmul_rn(u64_to_f32(S[4 + a]), inv));
+      }
+      c.weight = ldexpf(Wf, -kFixShift - min(mmin, 1 << 30));
       c.count = count;
       c.rep = g;
       c.pad = 0u;
@@ -958,40 +1001,36 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   mark(1);
   k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x,
                                                                        geo.count_chunks);
+  k_levels<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(2);
-  k_assign<DT><<<t.n_tiles, kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr, (float)out.unit_m);
+  k_assign<DT><<<t.n_tiles, kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr, (float)out.unit_m,
+                                                        geo.tiles);
   mark(3);
-  k_link<<<geo.emit_blocks, kThreads, 0, s>>>(t);
-  mark(4);
   k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
-  mark(5);
+  mark(4);
   k_scan<<<t.n_wblocks, 1024, 0, s>>>(t, out);
-  mark(6);
+  mark(5);
   k_emit<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
-  mark(7);
+  mark(6);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int n_tiles_for(const RigDev& rig) {
-  int n = 0;
-  for (int i = 0; i < rig.n_cams; ++i)
-    n += ((rig.cam[i].W + kTileW - 1) / kTileW) * ((rig.cam[i].H + kTileH - 1) / kTileH);
-  return n;
-}
-
-void fill_tiles(const RigDev& rig, TileDesc* out) {
+int fill_tile_index(const RigDev& rig, TileIndex* out) {
+  memset(out, 0, sizeof(*out));
+  out->n_cams = rig.n_cams;
+  out->k1 = rig.k1;
   int n = 0;
   for (int i = 0; i < rig.n_cams; ++i) {
-    const CamDev& c = rig.cam[i];
-    for (int y0 = 0; y0 < c.H; y0 += kTileH)
-      for (int x0 = 0; x0 < c.W; x0 += kTileW) {
-        TileDesc d;
-        d.cam = i; d.x0 = x0; d.y0 = y0; d.W = c.W; d.H = c.H; d.k1 = rig.k1; d.off = c.off;
-        out[n++] = d;
-      }
+    out->first[i] = n;
+    out->W[i] = rig.cam[i].W;
+    out->H[i] = rig.cam[i].H;
+    out->off[i] = rig.cam[i].off;
+    n += ((rig.cam[i].W + kTileW - 1) / kTileW) * ((rig.cam[i].H + kTileH - 1) / kTileH);
   }
+  out->first[rig.n_cams] = n;
+  return n;
 }
 
 void fill_block_consts(const RigDev& rig, BlockConst* out) {

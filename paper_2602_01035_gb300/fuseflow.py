@@ -94,7 +94,7 @@ EXPORTS = {
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
-FUSEFLOW_N_STAGES = 7
+FUSEFLOW_N_STAGES = 6
 
 _lib = None
 
