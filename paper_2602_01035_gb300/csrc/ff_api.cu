@@ -346,16 +346,13 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   auto take = [&](size_t bytes, size_t align) { o = align_up(o, align); size_t at = o; o += bytes; return at; };
   // (tile, cell) partials: at most one per gated pixel
   const unsigned max_partials = (unsigned)std::min<long long>(off, 0xfffffffell);
-  const size_t o_fkey = take(sizeof(unsigned long long) * ctx->max_slots, 256);
-  const size_t o_fhead = take(sizeof(unsigned) * ctx->max_slots, 256);
-  const size_t o_fmmin = take(sizeof(int) * ctx->max_slots, 256);
+  const size_t o_frec = take(sizeof(SlotRec) * ctx->max_slots, 256);
   const size_t o_fused = take(sizeof(unsigned) * ctx->max_slots, 256);
   const size_t o_coarse = take(sizeof(CoarseEntry) * ctx->ccap, 256);
   const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
   const size_t o_part = take(sizeof(Partial) * (size_t)max_partials, 256);
-  const size_t o_pnext = take(sizeof(unsigned) * (size_t)max_partials, 256);
   const size_t o_staged = take(sizeof(CellOut) * (size_t)ctx->max_cells, 256);
   const size_t o_wpre = take(sizeof(unsigned) * (size_t)n_words, 256);
   const size_t o_bsum = take(sizeof(unsigned) * (size_t)n_wblocks, 256);
@@ -372,6 +369,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   ctx->out_bytes = po;
 
   const int n_tiles = fill_tile_index(*rig, &ctx->geo.tiles);
+  ctx->geo.tiles.ahead = assign_resident_blocks() * sms;
   std::vector<BlockConst> bconst((size_t)n_cams);
   fill_block_consts(*rig, bconst.data());
   const size_t pray_at = align_up(sizeof(BlockConst) * (size_t)n_cams, 256);
@@ -386,9 +384,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   if (status == FUSEFLOW_OK) {
     char* b = static_cast<char*>(ctx->d_tables);
     Tables& t = ctx->tab;
-    t.fkey = reinterpret_cast<unsigned long long*>(b + o_fkey);
-    t.fhead = reinterpret_cast<unsigned*>(b + o_fhead);
-    t.fmmin = reinterpret_cast<int*>(b + o_fmmin);
+    t.frec = reinterpret_cast<SlotRec*>(b + o_frec);
     t.fused = reinterpret_cast<unsigned*>(b + o_fused);
     t.max_slots = ctx->max_slots;
     t.coarse = reinterpret_cast<CoarseEntry*>(b + o_coarse);
@@ -404,7 +400,6 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     t.bstats = reinterpret_cast<BlockStats*>(b + o_bst);
     t.n_bstats = n_bstats;
     t.part = reinterpret_cast<Partial*>(b + o_part);
-    t.pnext = reinterpret_cast<unsigned*>(b + o_pnext);
     t.max_partials = max_partials;
     t.staged = reinterpret_cast<CellOut*>(b + o_staged);
     t.wprefix = reinterpret_cast<unsigned*>(b + o_wpre);
@@ -651,17 +646,14 @@ constexpr size_t kSRig = 0;
 constexpr size_t kSRays = al256(kSRig + sizeof(RigDev));
 constexpr size_t kSBConst = al256(kSRays + sizeof(float2) * kStaticMaxRays);
 constexpr size_t kSPRay = al256(kSBConst + sizeof(BlockConst) * kMaxCams);
-constexpr size_t kSFKey = al256(kSPRay + sizeof(float4) * kStaticMaxPairRays);
-constexpr size_t kSFHead = al256(kSFKey + sizeof(unsigned long long) * kStaticSlots);
-constexpr size_t kSFMmin = al256(kSFHead + sizeof(unsigned) * kStaticSlots);
-constexpr size_t kSFused = al256(kSFMmin + sizeof(int) * kStaticSlots);
+constexpr size_t kSFRec = al256(kSPRay + sizeof(float4) * kStaticMaxPairRays);
+constexpr size_t kSFused = al256(kSFRec + sizeof(SlotRec) * kStaticSlots);
 constexpr size_t kSCoarse = al256(kSFused + sizeof(unsigned) * kStaticSlots);
 constexpr size_t kSCUsed = al256(kSCoarse + sizeof(CoarseEntry) * kStaticCoarse);
 constexpr size_t kSCnt = al256(kSCUsed + sizeof(unsigned) * kStaticCoarse);
 constexpr size_t kSBStats = al256(kSCnt + sizeof(FrameCounters) + sizeof(unsigned) * kStaticWords);
 constexpr size_t kSPart = al256(kSBStats + sizeof(BlockStats) * kStaticBStats);
-constexpr size_t kSPNext = al256(kSPart + sizeof(Partial) * kStaticMaxPartials);
-constexpr size_t kSStaged = al256(kSPNext + sizeof(unsigned) * kStaticMaxPartials);
+constexpr size_t kSStaged = al256(kSPart + sizeof(Partial) * kStaticMaxPartials);
 constexpr size_t kSWPre = al256(kSStaged + sizeof(CellOut) * kStaticMaxCells);
 constexpr size_t kSBSum = al256(kSWPre + sizeof(unsigned) * kStaticWords);
 constexpr size_t kStaticBytes = al256(kSBSum + sizeof(unsigned) * kStaticWBlocks);
@@ -713,9 +705,7 @@ void neighbour_table_fixed(const fuseflow_extrinsics* ex, int n, int k1, int32_t
 
 Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   Tables t{};
-  t.fkey = reinterpret_cast<unsigned long long*>(base + kSFKey);
-  t.fhead = reinterpret_cast<unsigned*>(base + kSFHead);
-  t.fmmin = reinterpret_cast<int*>(base + kSFMmin);
+  t.frec = reinterpret_cast<SlotRec*>(base + kSFRec);
   t.fused = reinterpret_cast<unsigned*>(base + kSFused);
   t.max_slots = kStaticSlots;
   t.coarse = reinterpret_cast<CoarseEntry*>(base + kSCoarse);
@@ -726,7 +716,6 @@ Tables static_tables(unsigned char* base, long long n_px, int n_bstats) {
   t.bstats = reinterpret_cast<BlockStats*>(base + kSBStats);
   t.n_bstats = n_bstats;
   t.part = reinterpret_cast<Partial*>(base + kSPart);
-  t.pnext = reinterpret_cast<unsigned*>(base + kSPNext);
   t.max_partials = kStaticMaxPartials;
   t.staged = reinterpret_cast<CellOut*>(base + kSStaged);
   t.wprefix = reinterpret_cast<unsigned*>(base + kSWPre);
@@ -803,6 +792,11 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   const int np = (int)(2ll * k1 * n_rays);
   Geometry geo{};
   const int n_tiles = fill_tile_index(rig, &geo.tiles);
+  {
+    int sm_count = 152;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    geo.tiles.ahead = assign_resident_blocks() * sm_count;
+  }
   fill_block_consts(rig, g_static_bconst);
   // pageable host -> device copies return once the host buffers have been read
   if (cudaMemcpyAsync(base + kSBConst, g_static_bconst, sizeof(BlockConst) * (size_t)n_cams,

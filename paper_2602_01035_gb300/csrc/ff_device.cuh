@@ -85,21 +85,32 @@ struct TileIndex {
   int first[kMaxCams + 1];
   int W[kMaxCams], H[kMaxCams];
   long long off[kMaxCams];       // global index of each camera's pixel (0, 0)
+  int pray[kMaxCams];            // float4 index of the camera's first pair ray: pair q's A
+                                 // starts at pray + 2 q (W + H), its B 2 W further
+  int per_cam;                   // tiles per camera when all cameras share W and H, else 0
+  int ahead;                     // tiles resident at once: block b prefetches tile b + ahead
 };
 
-// Per (tile, cell) partial result of the assign step; the link step pushes it onto its
-// cell's list (next[] holds the links).  Sums are exact integers in units of
-// 2^-(kFixShift + mmin) of the tile's own smallest weight exponent mmin; the reduce step
-// shifts them to the cell's smallest exponent.
+// Per (tile, cell) partial result of the assign step, pushed onto its cell's list when it
+// is written.  Sums are exact integers in units of 2^-(kFixShift + mmin) of the tile's own
+// smallest weight exponent mmin; the reduce step shifts them to the cell's smallest one.
 struct __align__(16) Partial {
   unsigned slot;                 // dense slot of the cell
   unsigned count;                // members in the tile
   int mmin;                      // smallest weight exponent m in the tile
-  unsigned pad;
+  unsigned next;                 // next partial of the same cell, kSlotNone at the end
   unsigned long long rep;        // max of ordered(C) << 32 | ~g
   unsigned long long s[7];       // sums of w, w frac_x, w frac_y, w frac_z, w r, w g, w b
 };
 static_assert(sizeof(Partial) == 80, "partial record layout");
+
+// Per dense cell slot: the cell's key, its list head and its smallest weight exponent, in
+// one 16-byte record so that the reduce step reads a single sector per cell.
+struct __align__(16) SlotRec {
+  unsigned long long key;
+  unsigned head;                 // last partial pushed, kSlotNone if none
+  int mmin;                      // smallest weight exponent over the cell's partials
+};
 
 // Coarse hash-table record: key, density count (Sec. II.5(1)c) and, once every count is
 // in, the level and first dense cell slot packed as level << 27 | base.

@@ -17,9 +17,7 @@ struct FramePtrs {               // one frame's caller-owned device images, per 
 
 struct Tables {                  // context-owned device scratch
   // cells: dense slots, coarse cell c owns [cbase(c), cbase(c) + 8^level(c))
-  unsigned long long* fkey;      // key of each used slot, max_slots entries
-  unsigned* fhead;               // first partial of each slot, kSlotNone if none
-  int* fmmin;                    // smallest weight exponent of each slot
+  SlotRec* frec;                 // key, list head and smallest exponent per slot
   unsigned* fused;               // used slots, in claim order
   unsigned max_slots;
   // coarse hash table (open addressing), ccap entries
@@ -30,7 +28,6 @@ struct Tables {                  // context-owned device scratch
   BlockStats* bstats;            // one per block of the coarse-count step
   int n_bstats;
   Partial* part;                 // (tile, cell) partials, max_partials entries
-  unsigned* pnext;               // list link of each partial, max_partials entries
   unsigned max_partials;
   CellOut* staged;               // fused cells by claim order, max_cells entries
   unsigned* bitmap;              // representative bitmap, one bit per pixel
@@ -79,6 +76,7 @@ cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cu
 
 // Host-side construction of the assign step's tile index and per-camera block constants
 // (caller-sized array of rig.n_cams entries) from the rig constants.
+int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
 int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);
 // ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages

@@ -33,6 +33,7 @@ constexpr int kCountPx = 8;                       // pixels per thread in the co
 constexpr int kCountBlockPx = kThreads * kCountPx;
 constexpr int kTileW = 32, kTileH = 16;           // assign/accum tile: 8 warps x 2 rows
 constexpr int kTilePx = kTileW * kTileH;
+constexpr int kPrayPerView = 2 * kTileW + 2 * kTileH;   // staged pair-ray float4 per view
 constexpr int kMaxProbe = 1 << 14;
 constexpr float kLn2H = 0.693147182464599609375f;         // float(ln 2)
 constexpr float kLn2L = -1.904654299957768e-09f;          // ln 2 - kLn2H
@@ -104,30 +105,30 @@ __global__ void __launch_bounds__(kThreads) k_levels(Tables t) {
   }
 }
 
-// Block-local open addressing (shared memory); returns the table position or -1.
+// Block-local open addressing (shared memory); returns the table position or -1, and sets
+// `fresh` when this call inserted the key.
 template <int TS, typename K>
-__device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe = TS) {
+__device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe, bool& fresh) {
   unsigned h = (unsigned)mix64((unsigned long long)key) & (TS - 1);
+  fresh = false;
   for (int probe = 0; probe < max_probe; ++probe) {
     const K cur = *static_cast<volatile K*>(&tab[h]);
     if (cur == key) return (int)h;
     if (cur == empty) {
       const K prev = atomicCAS(&tab[h], empty, key);
-      if (prev == empty || prev == key) return (int)h;
+      fresh = prev == empty;
+      if (fresh || prev == key) return (int)h;
     }
     h = (h + 1) & (TS - 1);
   }
   return -1;
 }
-
-// ------------------------------------------------------------------ block constants
-// The tile's camera, its K-1 neighbour pairs and the neighbour cameras, staged in shared
-// memory once per block (every pixel of a tile belongs to the same camera).
-__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes) {
-  int* d = static_cast<int*>(dst);
-  const int* s = static_cast<const int*>(src);
-  for (int i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
+template <int TS, typename K>
+__device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe = TS) {
+  bool fresh;
+  return local_pos<TS>(tab, empty, key, max_probe, fresh);
 }
+
 
 // ------------------------------------------------------------------ Eq. 4-7 per point
 // Exact floor(u + 1/2) for u = fx a_x / a_z + cx near a tie at integer r (a_z > 0):
@@ -147,17 +148,17 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 }
 
 // Sum over the K-1 neighbour views of d_ij^2 (Eq. 6) in depth units^2, as ff (sh, sl).
-// Pixel (x, y) of the block's camera at z-depth z; the transform into view j (Eq. 4) uses
-// the separable pair rays, so that a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff
-// product and one ff sum per component.  Views go in groups of kViewGroup: every view of
+// Pixel (lx, ly) of the block's tile at z-depth z; the transform into view j (Eq. 4) uses
+// the tile's separable pair rays staged in shared memory (s_pr), so that
+// a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff product and one ff sum per component.  Views go in groups of kViewGroup: every view of
 // a group is projected and its depth gather issued before any residual is formed, so the
 // gathers of a group overlap instead of following one another.
 constexpr int kViewGroup = 3;
 
 template <typename DT>
-__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const float4* __restrict__ pray,
+__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const float4* s_pr,
                                              const float2* __restrict__ rays,
-                                             const FramePtrs& fp, float z, int x, int y,
+                                             const FramePtrs& fp, float z, int lx, int ly,
                                              float& sh, float& sl, int& nview) {
   sh = 0.0f;
   sl = 0.0f;
@@ -178,8 +179,9 @@ __device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const
       if (q >= k1) continue;
       const PairDev& P = bc.pair[q];
       const CamDev& J = bc.nb[q];
-      const float4 a01 = __ldg(pray + P.ga + 2 * x), a2 = __ldg(pray + P.ga + 2 * x + 1);
-      const float4 b01 = __ldg(pray + P.gb + 2 * y), b2 = __ldg(pray + P.gb + 2 * y + 1);
+      const float4* pr = s_pr + q * kPrayPerView;
+      const float4 a01 = pr[lx], a2 = pr[kTileW + lx];
+      const float4 b01 = pr[2 * kTileW + ly], b2 = pr[2 * kTileW + kTileH + ly];
       ff_ray_affine(a01.x, a01.y, b01.x, b01.y, z, P.th[0], P.tl[0], ah[g][0], al[g][0]);
       ff_ray_affine(a01.z, a01.w, b01.z, b01.w, z, P.th[1], P.tl[1], ah[g][1], al[g][1]);
       ff_ray_affine(a2.x, a2.y, b2.x, b2.y, z, P.th[2], P.tl[2], ah[g][2], al[g][2]);
@@ -448,24 +450,46 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
 
 // ------------------------------------------------------------------ assign step
 constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
-constexpr int kAssignNL = kTilePx;         // distinct fine cells of a tile, at most
+// Distinct cells of a tile with shared-memory accumulators; the members of any further
+// cell (sparse, noisy tiles only) file one single-member partial each.
+constexpr int kAssignNL = kTilePx / 2;
+constexpr int kAssignBlocksPerSM = 4;      // registers (64) and shared memory allow four
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+static_assert(sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev)) <= 2 * 4 * kThreads,
+              "two words per thread copy a block's constants");
 constexpr size_t kSmBC = 0;
-constexpr size_t kSmFK = align16(kSmBC + sizeof(BlockConst));      // u32[TS] cell slots
-constexpr size_t kSmFI = align16(kSmFK + 4 * kAssignTS);           // int[TS] entry of a position
-constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64[NL] key of an entry
-constexpr size_t kSmES = align16(kSmEK + 8 * kAssignNL);           // u32[NL] slot of an entry
-constexpr size_t kSmAcc = align16(kSmES + 4 * kAssignNL);          // u32[14][NL] split sums
-constexpr size_t kSmCnt = align16(kSmAcc + 14 * 4 * kAssignNL);    // u32[NL] members
-constexpr size_t kSmCmax = align16(kSmCnt + 4 * kAssignNL);        // u32[NL] largest ordered C
-constexpr size_t kSmGmin = align16(kSmCmax + 4 * kAssignNL);       // u32[NL] lowest index at it
-constexpr size_t kSmMin = align16(kSmGmin + 4 * kAssignNL);        // int[NL] smallest exponent
-constexpr size_t kSmPid = align16(kSmMin + 4 * kAssignNL);         // u16[tile] gated pixels
+// per hash position (kAssignTS): cell slot, entry index, smallest weight exponent, largest
+// ordered C, member count; the last four are contiguous so that one loop clears them
+constexpr size_t kSmFK = align16(kSmBC + sizeof(BlockConst));      // u32 cell slot
+constexpr size_t kSmMinP = kSmFK + 4 * kAssignTS;                  // int smallest exponent
+constexpr size_t kSmCmaxP = kSmMinP + 4 * kAssignTS;               // u32 largest ordered C
+constexpr size_t kSmCntP = kSmCmaxP + 4 * kAssignTS;               // u32 members
+constexpr size_t kSmFI = align16(kSmCntP + 4 * kAssignTS);         // int entry of a position
+// per entry (kAssignNL): key, hash position, lowest index at the largest C, split sums
+constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64 key
+constexpr size_t kSmEP = align16(kSmEK + 8 * kAssignNL);           // u32 hash position
+constexpr size_t kSmGmin = align16(kSmEP + 4 * kAssignNL);         // u32 lowest index
+constexpr size_t kSmAcc = align16(kSmGmin + 4 * kAssignNL);        // u32[14][NL] split sums
+constexpr size_t kSmPid = align16(kSmAcc + 14 * 4 * kAssignNL);    // u16[tile] gated pixels
 constexpr size_t kSmZ = align16(kSmPid + 2 * kTilePx);             // f32[tile] their depth
 constexpr size_t kSmC = align16(kSmZ + 4 * kTilePx);               // f32[tile] confidence
 constexpr size_t kSmRGB = align16(kSmC + 4 * kTilePx);             // u32[tile] colour
-constexpr size_t kAssignSmem = align16(kSmRGB + 4 * kTilePx);
+constexpr size_t kSmPR = align16(kSmRGB + 4 * kTilePx);            // float4[K1][96] pair rays
+// dynamic shared memory of a launch with k1 neighbour views
+constexpr size_t assign_smem(int k1) { return kSmPR + 16 * (size_t)k1 * kPrayPerView; }
 constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
+
+// Writes partial p as record pi and pushes it onto its cell's list; true when it is the
+// cell's first partial of the frame (the caller then lists the cell).
+__device__ __forceinline__ bool file_partial(const Tables& t, Partial& p, unsigned long long key,
+                                             unsigned pi) {
+  SlotRec& rec = t.frec[p.slot];
+  rec.key = key;                                // the same value from every tile of the cell
+  atomicMin(&rec.mmin, p.mmin);
+  p.next = atomicExch(&rec.head, pi);           // list push
+  t.part[pi] = p;
+  return p.next == kSlotNone;
+}
 
 // rint(v) for 0 <= v < 2^37 as hi 2^22 + lo with lo in [0, 2^22], using 32-bit conversions
 // only: v - floor(v 2^-22) 2^22 is exact (both are multiples of ulp(v)), and adding the even
@@ -483,21 +507,38 @@ __device__ __forceinline__ ulonglong2 coarse_probe(const Tables& t, unsigned lon
   return __ldg(reinterpret_cast<const ulonglong2*>(&t.coarse[h]));
 }
 
+// Camera and first pixel of tile T: a division when every camera has the same size, else
+// a binary search of the per-camera tile ranges (constant bank).
+__device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, int& x0, int& y0) {
+  if (ti.per_cam) {
+    cam = T / ti.per_cam;
+  } else {
+    cam = 0;
+    for (int lo = 0, hi = ti.n_cams - 1; lo <= hi;) {
+      const int mid = (lo + hi) >> 1;
+      if (ti.first[mid] <= T) { cam = mid; lo = mid + 1; } else { hi = mid - 1; }
+    }
+  }
+  const int local = T - ti.first[cam], tiles_x = (ti.W[cam] + kTileW - 1) / kTileW;
+  x0 = (local % tiles_x) * kTileW;
+  y0 = (local / tiles_x) * kTileH;
+}
+
 template <typename DT>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, kAssignBlocksPerSM)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m, TileIndex ti) {
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
   unsigned* s_fk = reinterpret_cast<unsigned*>(smem + kSmFK);
+  int* s_minp = reinterpret_cast<int*>(smem + kSmMinP);
+  unsigned* s_cmaxp = reinterpret_cast<unsigned*>(smem + kSmCmaxP);
+  unsigned* s_cntp = reinterpret_cast<unsigned*>(smem + kSmCntP);
   int* s_fi = reinterpret_cast<int*>(smem + kSmFI);
   unsigned long long* s_ek = reinterpret_cast<unsigned long long*>(smem + kSmEK);
-  unsigned* s_es = reinterpret_cast<unsigned*>(smem + kSmES);
-  unsigned* s_acc = reinterpret_cast<unsigned*>(smem + kSmAcc);
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(smem + kSmCnt);
-  unsigned* s_cmax = reinterpret_cast<unsigned*>(smem + kSmCmax);
+  unsigned* s_ep = reinterpret_cast<unsigned*>(smem + kSmEP);
   unsigned* s_gmin = reinterpret_cast<unsigned*>(smem + kSmGmin);
-  int* s_min = reinterpret_cast<int*>(smem + kSmMin);
+  unsigned* s_acc = reinterpret_cast<unsigned*>(smem + kSmAcc);
   unsigned short* s_pid = reinterpret_cast<unsigned short*>(smem + kSmPid);
   float* s_z = reinterpret_cast<float*>(smem + kSmZ);
   float* s_c = reinterpret_cast<float*>(smem + kSmC);
@@ -505,28 +546,78 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   __shared__ unsigned s_n, s_base, s_ng;
 
   const RigDev& rig = *rigp;
-  // this block's tile: binary search of the per-camera tile ranges (constant bank)
-  int cam = 0;
-  for (int lo = 0, hi = ti.n_cams - 1; lo <= hi;) {
-    const int mid = (lo + hi) >> 1;
-    if (ti.first[mid] <= (int)blockIdx.x) { cam = mid; lo = mid + 1; } else { hi = mid - 1; }
-  }
+  int cam, x0, y0;
+  tile_of(ti, (int)blockIdx.x, cam, x0, y0);
   const int W = ti.W[cam], H = ti.H[cam], k1 = ti.k1;
   struct { int x0, y0; long long off; } td;
-  {
-    const int local = (int)blockIdx.x - ti.first[cam], tiles_x = (W + kTileW - 1) / kTileW;
-    td.x0 = (local % tiles_x) * kTileW;
-    td.y0 = (local / tiles_x) * kTileH;
-    td.off = ti.off[cam];
-  }
+  td.x0 = x0;
+  td.y0 = y0;
+  td.off = ti.off[cam];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // warm L2 with the images of the tile that starts when this wave of blocks has finished
+  if (threadIdx.x < 4 * kTileH && (int)blockIdx.x + ti.ahead < t.n_tiles) {
+    int pc, px0, py0;
+    tile_of(ti, (int)blockIdx.x + ti.ahead, pc, px0, py0);
+    const int row = py0 + (threadIdx.x & (kTileH - 1)), kind = threadIdx.x / kTileH;
+    if (row < ti.H[pc]) {                     // every address lies inside its image
+      const long long li = (long long)row * ti.W[pc] + px0;
+      const long long last = (long long)row * ti.W[pc] + min(px0 + kTileW, ti.W[pc]) - 1;
+      const char* a = kind == 0 ? static_cast<const char*>(fp.depth[pc]) + li * sizeof(DT)
+                    : kind == 1 ? reinterpret_cast<const char*>(fp.conf[pc] + li)
+                    : reinterpret_cast<const char*>(fp.rgb[pc]) + 3 * (kind == 3 ? last : li);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+  }
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
   const float* __restrict__ cf = fp.conf[cam];
   const uint8_t* __restrict__ col = fp.rgb[cam];
-  // issue the tile's image loads and the constant copy together (one round trip)
+  // issue the constant-block loads (L2) and the tile's image loads (HBM) before waiting
+  // on either: the words of cam, pair[0, k1) and nb[0, k1) of this camera's BlockConst
+  constexpr int kCamW = sizeof(CamDev) / 4, kPairW = sizeof(PairDev) / 4;
+  constexpr int kNbAt = (int)(offsetof(BlockConst, nb) / 4), kPairAt = (int)(offsetof(BlockConst, pair) / 4);
+  const int n_cw = kCamW + k1 * (kPairW + kCamW);
+  const int* gsrc = reinterpret_cast<const int*>(&t.bconst[cam]);
+  int cwv[2], cwi[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int w = threadIdx.x + r * kThreads;
+    cwi[r] = w < kCamW ? w
+           : w < kCamW + k1 * kPairW ? kPairAt + (w - kCamW)
+           : w < n_cw ? kNbAt + (w - kCamW - k1 * kPairW) : -1;
+    cwv[r] = cwi[r] >= 0 ? __ldg(gsrc + cwi[r]) : 0;
+  }
+  // the tile's pair rays (Eq. 4): per view, A of its 32 columns and B of its 16 rows, each
+  // as two float4 planes: [A first halves | A second halves | B first | B second]
+  constexpr int kPrayLoads = (kMaxK1 * kPrayPerView + kThreads - 1) / kThreads;
+  float4 prv[kPrayLoads];
+  int pri[kPrayLoads];
+  {
+    const int Wp = W, Hp = H;
+#pragma unroll
+    for (int r = 0; r < kPrayLoads; ++r) {
+      const int idx = threadIdx.x + r * kThreads;
+      pri[r] = -1;
+      prv[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (idx >= k1 * kPrayPerView) continue;
+      const int q = idx / kPrayPerView, o = idx - q * kPrayPerView;
+      const int base = ti.pray[cam] + 2 * q * (Wp + Hp);
+      int src = -1;
+      if (o < 2 * kTileW) {                                        // A: plane o / 32
+        const int c = td.x0 + (o & (kTileW - 1));
+        if (c < Wp) src = base + 2 * c + o / kTileW;
+      } else {                                                     // B: plane (o - 64) / 16
+        const int rr = o - 2 * kTileW, row = td.y0 + (rr & (kTileH - 1));
+        if (row < Hp) src = base + 2 * Wp + 2 * row + rr / kTileH;
+      }
+      if (src >= 0) {
+        prv[r] = __ldg(t.pray + src);
+        pri[r] = idx;
+      }
+    }
+  }
   DT Dk[2];
   float ckv[2];
-  unsigned rgbk[2] = {0u, 0u};
+  uint8_t cb[2][3];
   bool inimg[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -534,19 +625,30 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     inimg[k] = x < W && y < H;
     Dk[k] = (DT)0;
     ckv[k] = 0.0f;
+    cb[k][0] = cb[k][1] = cb[k][2] = 0;
     if (inimg[k]) {
       const long long li = (long long)y * W + x;
       Dk[k] = dep[li];
       ckv[k] = cf[li];
       const uint8_t* px = col + 3 * li;
-      rgbk[k] = (unsigned)px[0] | ((unsigned)px[1] << 8) | ((unsigned)px[2] << 16);
+      cb[k][0] = px[0];
+      cb[k][1] = px[1];
+      cb[k][2] = px[2];
     }
   }
-  const BlockConst& gbc = t.bconst[cam];
-  copy_words(&bc.cam, &gbc.cam, sizeof(CamDev));
-  copy_words(bc.pair, gbc.pair, k1 * (int)sizeof(PairDev));
-  copy_words(bc.nb, gbc.nb, k1 * (int)sizeof(CamDev));
-  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) s_fk[i] = kSlotNone;
+  int* sdst = reinterpret_cast<int*>(&bc);
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (cwi[r] >= 0) sdst[cwi[r]] = cwv[r];
+  float4* s_pr = reinterpret_cast<float4*>(smem + kSmPR);
+#pragma unroll
+  for (int r = 0; r < kPrayLoads; ++r)
+    if (pri[r] >= 0) s_pr[pri[r]] = prv[r];
+  // clear the per-position arrays: slot none, exponent INT_MAX, largest C 0, count 0
+  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
+    const unsigned v = i < kAssignTS / 4 ? kSlotNone : i < kAssignTS / 2 ? (unsigned)INT_MAX : 0u;
+    reinterpret_cast<uint4*>(smem + kSmFK)[i] = make_uint4(v, v, v, v);
+  }
   if (threadIdx.x == 0) { s_n = 0; s_ng = 0; }
   __syncthreads();
 
@@ -579,12 +681,28 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       s_pid[pos] = (unsigned short)(row * kTileW + lane);
       s_z[pos] = Depth<DT>::z(Dk[k]);
       s_c[pos] = ckv[k];
-      s_rgb[pos] = rgbk[k];
+      s_rgb[pos] = (unsigned)cb[k][0] | ((unsigned)cb[k][1] << 8) | ((unsigned)cb[k][2] << 16);
     }
   }
   __syncthreads();
   const int n_g = (int)s_ng;
   const CamDev& C = bc.cam;
+
+  // the second point's coarse record: start its lookup now (into L1), so that it arrives
+  // while the first point is processed
+  {
+    const int i = threadIdx.x + kThreads;
+    if (i < n_g) {
+      const int pid = s_pid[i];
+      const int x = td.x0 + (pid & (kTileW - 1)), y = td.y0 + pid / kTileW;
+      float P[3], r[3];
+      world_point(C, s_z[i], __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
+      if (grid_coords(rig, P, r)) {
+        const unsigned h = (unsigned)mix64(coarse_key(r)) & t.cmask;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(&t.coarse[h]));
+      }
+    }
+  }
 
   // (a) Eq. 8, (b) Eq. 4-7 and 10, (c) Sec. II.5(1)d-e for each gated point
   bool has[2] = {false, false};
@@ -616,7 +734,8 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     float sh = 0.0f, sl = 0.0f, eh = 0.0f, el = 0.0f;
     int nview = 0;
     if (rig.use_cons && k1 > 0) {
-      residual_sum<DT>(bc, k1, t.pray, rays, fp, z, x, y, sh, sl, nview);
+      residual_sum<DT>(bc, k1, reinterpret_cast<const float4*>(smem + kSmPR), rays, fp, z,
+                       x - td.x0, y - td.y0, sh, sl, nview);
       fast_two_sum(sh, sl, sh, sl);
       two_prod(sh, rig.einv_h, eh, el);                               // Eq. 7 exponent
       el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
@@ -666,52 +785,47 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
         has[j] = false;
       } else {
         fkey[j] = fk;
-        hpos[j] = local_pos<kAssignTS>(s_fk, kSlotNone, cbase + local);
-        if (hpos[j] < 0) { has[j] = false; atomicOr(&t.cnt->error, kErrSlots); }
+        bool fresh;
+        const int h = local_pos<kAssignTS>(s_fk, kSlotNone, cbase + local, kAssignTS, fresh);
+        hpos[j] = h;
+        if (h < 0) {
+          has[j] = false;
+          atomicOr(&t.cnt->error, kErrSlots);
+        } else {
+          if (fresh) {                          // the cell's entry: index and accumulators
+            const int e = (int)atomicAdd(&s_n, 1u);
+            s_fi[h] = e;
+            if (e < kAssignNL) {
+              s_ek[e] = fk;
+              s_ep[e] = (unsigned)h;
+              s_gmin[e] = 0xffffffffu;
+#pragma unroll
+              for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
+            }
+          }
+          // Sec. II.5(2)a: members, largest C, smallest weight exponent
+          atomicAdd(&s_cntp[h], 1u);
+          atomicMax(&s_cmaxp[h], cord[j]);
+          atomicMin(&s_minp[h], mexp[j]);
+        }
       }
     }
     if (trace && tr.key) tr.key[gi[j]] = has[j] ? fkey[j] : kKeyEmpty;
   }
   __syncthreads();
-  // compact the tile's cells: entry index per hash position
-  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
-    const unsigned slot = s_fk[i];
-    if (slot == kSlotNone) continue;
-    const int e = (int)atomicAdd(&s_n, 1u);
-    s_fi[i] = e;
-    s_es[e] = slot;
-    s_cnt[e] = 0u;
-    s_cmax[e] = 0u;
-    s_gmin[e] = 0xffffffffu;
-    s_min[e] = INT_MAX;
-#pragma unroll
-    for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
-  }
-  __syncthreads();
   // reserve the tile's partial records now; the index is needed only at the end
-  const unsigned n_local = s_n;
+  const unsigned n_local = min(s_n, (unsigned)kAssignNL);
   unsigned base_pi = 0u;
   if (threadIdx.x == 0) base_pi = atomicAdd(&t.cnt->n_partials, n_local);
-  // (d) Sec. II.5(2)a: members, largest C, smallest weight exponent
-  int ent[2] = {0, 0};
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    if (!has[j]) continue;
-    ent[j] = s_fi[hpos[j]];
-    s_ek[ent[j]] = fkey[j];                     // every member writes the same key
-    atomicAdd(&s_cnt[ent[j]], 1u);
-    atomicMax(&s_cmax[ent[j]], cord[j]);
-    atomicMin(&s_min[ent[j]], mexp[j]);
-  }
-  __syncthreads();
   // representative: lowest pixel index among the largest C; Eq. 11 sums at the tile's
   // scale 2^-(36 + mmin_tile), each 64-bit term split in two native 32-bit atomics
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     if (!has[j]) continue;
-    const int e = ent[j];
-    if (cord[j] == s_cmax[e]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
-    const int sh = mexp[j] - s_min[e];
+    const int h = hpos[j], e = s_fi[h];
+    const bool alone = e >= kAssignNL;
+    if (!alone && cord[j] == s_cmaxp[h]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
+    const int sh = alone ? 0 : mexp[j] - s_minp[h];
     const float w = sh > 62 ? 0.0f : __fmul_rn(mu[j], pow2f(kFixShift - sh));
     const unsigned rgb = s_rgb[threadIdx.x + j * kThreads];
     float v[7];
@@ -721,39 +835,68 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       v[4 + a] = __fmul_rn(w, (float)((rgb >> (8 * a)) & 0xffu) * 0.00390625f);
+    if (!alone) {
 #pragma unroll
-    for (int a = 0; a < 7; ++a) {
-      unsigned lo, hi;
-      split_round(v[a], lo, hi);
-      atomicAdd(&s_acc[(2 * a) * kAssignNL + e], lo);
-      atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], hi);
+      for (int a = 0; a < 7; ++a) {
+        unsigned lo, hi;
+        split_round(v[a], lo, hi);
+        atomicAdd(&s_acc[(2 * a) * kAssignNL + e], lo);
+        atomicAdd(&s_acc[(2 * a + 1) * kAssignNL + e], hi);
+      }
+    } else {                                    // a single-member partial of its own
+      Partial p;
+      p.slot = s_fk[hpos[j]];
+      p.count = 1u;
+      p.mmin = mexp[j];
+      p.rep = ((unsigned long long)cord[j] << 32) | (unsigned)(~(unsigned)gi[j]);
+#pragma unroll
+      for (int a = 0; a < 7; ++a) {
+        unsigned lo, hi;
+        split_round(v[a], lo, hi);
+        p.s[a] = ((unsigned long long)hi << kLoBits) + lo;
+      }
+      const unsigned pi = atomicAdd(&t.cnt->n_partials, 1u);
+      if (pi >= t.max_partials) {
+        atomicOr(&t.cnt->error, kErrPartials);
+      } else if (file_partial(t, p, fkey[j], pi)) {
+        const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
+        if (n < t.max_slots) t.fused[n] = p.slot;
+      }
     }
   }
   if (threadIdx.x == 0) s_base = base_pi;
   __syncthreads();
-  // one partial record per (tile, cell); the link step files it under its cell
-  for (int e = threadIdx.x; e < (int)n_local; e += kThreads) {
-    const unsigned pi = s_base + (unsigned)e;
-    if (pi >= t.max_partials) { atomicOr(&t.cnt->error, kErrPartials); continue; }
-    Partial p;
-    p.slot = s_es[e];
-    p.count = s_cnt[e];
-    p.mmin = s_min[e];
-    p.pad = 0u;
-    t.fkey[p.slot] = s_ek[e];                   // the same value from every tile of the cell
-    p.rep = ((unsigned long long)s_cmax[e] << 32) | (unsigned)(~s_gmin[e]);
+  // one partial record per (tile, cell), pushed onto its cell's list
+  for (int e0 = 0; e0 < (int)n_local; e0 += kThreads) {
+    const int e = e0 + threadIdx.x;
+    bool first = false;
+    unsigned slot = 0u;
+    if (e < (int)n_local) {
+      const unsigned pi = s_base + (unsigned)e;
+      if (pi >= t.max_partials) {
+        atomicOr(&t.cnt->error, kErrPartials);
+      } else {
+        const unsigned h = s_ep[e];
+        Partial p;
+        p.slot = slot = s_fk[h];
+        p.count = s_cntp[h];
+        p.mmin = s_minp[h];
+        p.rep = ((unsigned long long)s_cmaxp[h] << 32) | (unsigned)(~s_gmin[e]);
 #pragma unroll
-    for (int a = 0; a < 7; ++a)
-      p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
-               s_acc[(2 * a) * kAssignNL + e];
-    t.part[pi] = p;
-    // file the partial under its cell: list push, smallest exponent, first-claim of the cell
-    atomicMin(&t.fmmin[p.slot], p.mmin);
-    const unsigned prev = atomicExch(&t.fhead[p.slot], pi);
-    t.pnext[pi] = prev;
-    if (prev == kSlotNone) {
-      const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
-      if (n < t.max_slots) t.fused[n] = p.slot;
+        for (int a = 0; a < 7; ++a)
+          p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
+                   s_acc[(2 * a) * kAssignNL + e];
+        first = file_partial(t, p, s_ek[e], pi);
+      }
+    }
+    // one counter update per warp for the cells claimed in it
+    const unsigned claim = __ballot_sync(0xffffffffu, first);
+    unsigned nb = 0u;
+    if (lane == 0 && claim) nb = atomicAdd(&t.cnt->n_cells, (unsigned)__popc(claim));
+    nb = __shfl_sync(0xffffffffu, nb, 0);
+    if (first) {
+      const unsigned n = nb + __popc(claim & ((1u << lane) - 1u));
+      if (n < t.max_slots) t.fused[n] = slot;
     }
   }
 }
@@ -772,9 +915,10 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < n_cells) {
       const unsigned slot = t.fused[i];
-      const unsigned long long key = t.fkey[slot];
-      const unsigned head = t.fhead[slot];
-      const int mmin = t.fmmin[slot];
+      const SlotRec rec = t.frec[slot];
+      const unsigned long long key = rec.key;
+      const unsigned head = rec.head;
+      const int mmin = rec.mmin;
       unsigned count = 0u, steps = 0u;
       unsigned long long rep = 0ull;
       unsigned long long S[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
@@ -785,7 +929,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
         const int sh = P.mmin - mmin;          // shift to the cell's smallest exponent
 #pragma unroll
         for (int a = 0; a < 7; ++a) S[a] += sh < 64 ? (P.s[a] >> sh) : 0ull;
-        p = t.pnext[p];
+        p = P.next;
       }
       if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
       const unsigned g = head != kSlotNone ? ~(unsigned)(rep & 0xffffffffull) : 0xffffffffu;
@@ -811,8 +955,9 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
         t.staged[i] = c;
         if (head != kSlotNone) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));
       }
-      t.fhead[slot] = kSlotNone;                // ready for the next frame
-      t.fmmin[slot] = INT_MAX;
+      // ready for the next frame: head = none, mmin = INT_MAX (one 8-byte store)
+      reinterpret_cast<unsigned long long*>(&t.frec[slot])[1] =
+          ((unsigned long long)(unsigned)INT_MAX << 32) | kSlotNone;
     }
     if (i < n_coarse) {
       const unsigned cs = t.cused[i];
@@ -972,9 +1117,9 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   const unsigned n = max(fcap, ccap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < fcap) {
-      t.fkey[i] = kKeyEmpty;
-      t.fhead[i] = kSlotNone;
-      t.fmmin[i] = INT_MAX;
+      t.frec[i].key = kKeyEmpty;
+      t.frec[i].head = kSlotNone;
+      t.frec[i].mmin = INT_MAX;
     }
     if (i < ccap) {
       t.coarse[i].key = kKeyEmpty;
@@ -990,7 +1135,7 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   static bool attr_set = false;
   if (!attr_set) {
     const cudaError_t e = cudaFuncSetAttribute(k_assign<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kAssignSmem);
+                                               (int)assign_smem(kMaxK1));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1003,7 +1148,7 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                                                                        geo.count_chunks);
   k_levels<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(2);
-  k_assign<DT><<<t.n_tiles, kThreads, kAssignSmem, s>>>(rig, rays, fp, t, tr, (float)out.unit_m,
+  k_assign<DT><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(rig, rays, fp, t, tr, (float)out.unit_m,
                                                         geo.tiles);
   mark(3);
   k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
@@ -1017,6 +1162,8 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
 
 }  // namespace
 
+int assign_resident_blocks() { return kAssignBlocksPerSM; }
+
 int fill_tile_index(const RigDev& rig, TileIndex* out) {
   memset(out, 0, sizeof(*out));
   out->n_cams = rig.n_cams;
@@ -1027,9 +1174,15 @@ int fill_tile_index(const RigDev& rig, TileIndex* out) {
     out->W[i] = rig.cam[i].W;
     out->H[i] = rig.cam[i].H;
     out->off[i] = rig.cam[i].off;
+    out->pray[i] = rig.k1 > 0 ? rig.pair[rig.cam[i].pair0].ga : 0;
     n += ((rig.cam[i].W + kTileW - 1) / kTileW) * ((rig.cam[i].H + kTileH - 1) / kTileH);
   }
   out->first[rig.n_cams] = n;
+  bool same = true;
+  for (int i = 1; i < rig.n_cams; ++i)
+    same = same && rig.cam[i].W == rig.cam[0].W && rig.cam[i].H == rig.cam[0].H;
+  out->per_cam = same && rig.n_cams > 0 ? out->first[1] : 0;
+  out->ahead = 1 << 30;                          // no prefetch unless the caller sets it
   return n;
 }
 

@@ -97,6 +97,20 @@ def test_sigma_and_levels(ffmod, oracle_mod):
                       {"sigma_m": 0.005, "n_min": 8, "max_level": 6, "coarse_cell_m": 0.5})
 
 
+def test_sparse_tiles_overflow_the_shared_accumulators(ffmod, oracle_mod):
+    """Depths scattered over 0.5-40 m put nearly every pixel of a 32x16 tile in a cell of
+    its own, past the 256 shared accumulators of a tile: those members file alone."""
+    rig = S.tiny_rig(n=3, width=96, height=48)
+    rng = np.random.default_rng(11)
+    z = [rng.integers(500, 40000, size=(48, 96), dtype=np.uint16) for _ in range(3)]
+    c = [rng.uniform(0.61, 1.0, size=(48, 96)).astype(np.float32) for _ in range(3)]
+    col = [rng.integers(0, 256, size=(48, 96, 3), dtype=np.uint8) for _ in range(3)]
+    rep, gpu, _ = _fuse_and_compare(ffmod, oracle_mod, rig, S.Frame(z, c, col),
+                                    {"max_level": 6, "n_min": 1})
+    assert gpu["stats"]["n_cells"] > 0.9 * gpu["stats"]["n_gated"]
+    assert rep["n_cells_matched"] > 10000
+
+
 def test_empty_and_all_gated_out(ffmod, oracle_mod):
     rig = S.tiny_rig(n=2, width=40, height=30)
     z = [np.zeros((30, 40), np.uint16) for _ in range(2)]
