@@ -173,6 +173,23 @@ def traffic_table():
         return {}
 
 
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Duration of the slowest rank's timed region (the job ends with it)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -226,17 +243,12 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     status, st = ff.stats(sh, check=False)
     ok_status = status == F.FUSEFLOW_OK
 
-    total_frames = world * args.steps * FPS
-    value = total_frames * px / (ms / 1e3)
-    fps = total_frames / (ms / 1e3)
+    value = job_rate(args.steps * FPS * px, world, ms)
+    fps = job_rate(args.steps * FPS, world, ms)
 
     # ------------------------------------------------------------ per-frame latency (plain path)
     lat = []
