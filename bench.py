@@ -40,6 +40,11 @@ def parse():
     ap.add_argument("--pool", type=int, default=8, help="distinct frames cycled (> L2 in total)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-frames", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=4,
+                    help="frames in flight on separate streams for the batched line")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of the Poisson arrival trace of the served/plain comparison")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -250,6 +255,51 @@ def run_ours(args, rank, world, local_rank):
     value = job_rate(args.steps * FPS * px, world, ms)
     fps = job_rate(args.steps * FPS, world, ms)
 
+    # ------------------------------------------------------------ batched: frames in flight
+    # the same frames through `slots` contexts on as many streams, frame k on slot k % slots
+    batched = None
+    if args.slots > 1:
+        B = args.slots
+        ctxs = [ff] + [F.FuseFlow(rig) for _ in range(B - 1)]
+        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(B - 1)]
+
+        def batched_step():
+            for i in range(FPS):
+                t = dtensors[i % len(dtensors)]
+                F.fuseflow_fuse_frame(ctxs[i % B].ctx, t[3], t[4], t[5], streams[i % B].cuda_stream)
+
+        def run_batched(n_steps):
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for s_ in streams[1:]:
+                s_.wait_event(start)
+            for _ in range(n_steps):
+                batched_step()
+            for s_ in streams[1:]:
+                ev = torch.cuda.Event()
+                ev.record(s_)
+                stream.wait_event(ev)
+            stop.record(stream)
+            torch.cuda.synchronize(dev)
+            return start.elapsed_time(stop)
+
+        run_batched(max(args.warmup, 1))
+        if world > 1:
+            torch.distributed.barrier()
+        bms = max_over_ranks(run_batched(args.steps), world, dev)
+        bst = [c.stats(stream.cuda_stream if k == 0 else streams[k].cuda_stream, check=False)[0]
+               for k, c in enumerate(ctxs)]
+        batched = {"slots": B, "value": round(job_rate(args.steps * FPS * px, world, bms), 1),
+                   "unit": "px/s", "frames_per_s": round(job_rate(args.steps * FPS, world, bms), 2),
+                   "ms_per_step": round(bms / args.steps, 4),
+                   "vs_plain": round(ms / bms, 4),
+                   "status_ok": all(x == F.FUSEFLOW_OK for x in bst),
+                   "path": f"{B} contexts on {B} streams, frame k on slot k mod {B}; same frames, "
+                           f"CUDA events around the step"}
+        for c in ctxs[1:]:
+            c.close()
+
     # ------------------------------------------------------------ per-frame latency (plain path)
     lat = []
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -345,6 +395,11 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": int(d2h / n_e2e * FPS),
            "frames_timed": n_e2e, "entry_point": "fuseflow_fuse_frame_host"}
 
+    # ------------------------------------------------------------ served vs plain
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(args, dev)
+
     # ------------------------------------------------------------ CPU baseline (oracle)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -367,6 +422,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "path_roofline": path_roof,
         "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "stage_roofline": stages,
+        "batched": batched, "serving": serving,
         "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
         "cells_per_frame": int(n_cells), "status_ok": ok_status,
         "clocks": clocks, "cpu_baseline": cpu,
@@ -376,6 +432,82 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- serving
+SERVE_BUDGET = 40 << 30          # HBM budget of the served rigs' slots (bytes)
+
+
+def run_serving(args, dev):
+    """Served vs plain on one seeded Poisson trace over 12 rigs of 2-24 cameras at
+    320x240 to 1920x1080 (15-60 fps per rig), frames from pinned host memory."""
+    import multiprocessing as mp
+    import numpy as np
+    import torch
+    from paper_2602_01035_gb300 import fuseflow as F
+    from paper_2602_01035_gb300 import scenes as S
+    from paper_2602_01035_gb300 import serving as SV
+
+    rigs, _ = S.serving_rigs()
+    n = len(rigs)
+    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
+        frames = pool.map(S.serving_frame, range(n))
+    rng = np.random.default_rng(5999 + 2)
+    rates = rng.uniform(15.0, 60.0, size=n)
+    trace = SV.poisson_trace(rates, args.serve_seconds, seed=5999 + 3)
+    px = [r.n_pixels for r in rigs]
+    pinned = [SV.pinned_frame(f) for f in frames]
+    caps = [max(65536, p // 16) for p in px]
+
+    srv = SV.Server(SERVE_BUDGET)
+    rids, slots = [], []
+    for r, rig in enumerate(rigs):
+        for k in (2, 1):
+            try:
+                rids.append(srv.add_rig(rig, n_slots=k, max_cells=caps[r]))
+                slots.append(k)
+                break
+            except F.FuseFlowError:
+                if k == 1:
+                    raise
+    from collections import deque
+    outs = [deque(SV.HostCloud(caps[r]) for _ in range(slots[r] + 1)) for r in range(n)]
+    # warm-up: one frame per rig
+    for r in range(n):
+        buf = outs[r].popleft()
+        srv.submit(rids[r], pinned[r], buf)
+        outs[r].append(buf)
+    srv.drain()
+    served = SV.replay_served(srv, rids, pinned, outs, trace, px)
+    sat_trace = [(0.0, r) for _, r in trace]
+    served_sat = SV.replay_served(srv, rids, pinned, outs, sat_trace, px)
+    srv_bytes = srv.device_bytes()
+    srv.close()
+
+    ctxs = [F.FuseFlow(rig, max_cells=caps[r]) for r, rig in enumerate(rigs)]
+    plain_outs = [SV.HostCloud(caps[r]) for r in range(n)]
+    sh = torch.cuda.current_stream(dev).cuda_stream
+    for r in range(n):
+        F.fuseflow_fuse_frame_host(ctxs[r].ctx, pinned[r]["depth"], pinned[r]["conf"],
+                                   pinned[r]["rgb"], plain_outs[r].c.pos, plain_outs[r].c.rgb,
+                                   plain_outs[r].c.weight, plain_outs[r].c.count,
+                                   plain_outs[r].c.rep, plain_outs[r].c.key, sh)
+    plain = SV.replay_plain([c.ctx for c in ctxs], pinned, plain_outs, trace, px, sh)
+    plain_sat = SV.replay_plain([c.ctx for c in ctxs], pinned, plain_outs, sat_trace, px, sh)
+    for c in ctxs:
+        c.close()
+    return {
+        "workload": f"{n} rigs of 2-24 cameras, 320x240 to 1920x1080 uint16, Poisson arrivals at "
+                    f"15-60 fps per rig for {args.serve_seconds:g} s ({len(trace)} frames, "
+                    f"{sum(px) / 1e6:.1f} Mpx per round of all rigs); frames from pinned host memory, "
+                    f"results into pinned host arrays; one rendered frame per rig, resubmitted",
+        "served": dict(served, slots_per_rig=slots, hbm_bytes=int(srv_bytes), budget=SERVE_BUDGET),
+        "plain": dict(plain, path="one fuseflow_fuse_frame_host call at a time, arrival order"),
+        "saturated": {"served_frames_per_s": served_sat["frames_per_s"],
+                      "plain_frames_per_s": plain_sat["frames_per_s"],
+                      "served_px_per_s": served_sat["px_per_s"], "plain_px_per_s": plain_sat["px_per_s"],
+                      "note": "the same frames, all arrived at t = 0"},
+    }
 
 
 # ----------------------------------------------------------------------------- oracle timing

@@ -209,6 +209,74 @@ int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_e
                                float *weight, uint32_t *count, uint32_t *rep, uint64_t *key,
                                fuseflow_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------------------------
+ * Serving: several rigs, frames arriving from host memory, continuous batching.
+ *
+ * The paper fuses the frames of one rig as a real-time stream (Sec. I, Sec. II.1); a
+ * server here keeps several rigs resident on one GPU and overlaps their frames.  Each
+ * rig gets n_slots frame slots, each with its own device tables, input staging buffers
+ * and stream; the slots of all rigs are allocated up front against an HBM budget.  A
+ * submitted frame starts at once when one of its rig's slots is free, otherwise it waits
+ * in the rig's FIFO and starts as soon as fuseflow_server_poll finds a slot finished, so
+ * the copies and kernels of frames of different rigs and slots overlap on the device.
+ * Results do not depend on the mix: every frame runs the same kernels on its own tables.
+ * Not thread-safe: drive one server from one host thread.
+ * ------------------------------------------------------------------------------------ */
+typedef struct fuseflow_server fuseflow_server;
+
+/* Caller-owned HOST output arrays for one frame (pinned memory, e.g. cudaHostAlloc;
+ * each sized for `capacity` cells; any array pointer may be NULL).  The first n_cells
+ * cells are written, in the order of fuseflow_cloud, before the frame completes. */
+typedef struct {
+    float *pos;             /* [capacity][3] */
+    float *rgb;             /* [capacity][3] */
+    float *weight;          /* [capacity] */
+    uint32_t *count;        /* [capacity] */
+    uint32_t *rep;          /* [capacity] */
+    uint64_t *key;          /* [capacity] */
+    int64_t capacity;
+} fuseflow_host_cloud;
+
+/* One finished frame, reported by fuseflow_server_poll. */
+typedef struct {
+    int64_t request;        /* id returned by fuseflow_server_submit */
+    int32_t rig;            /* rig id */
+    int32_t status;         /* as fuseflow_read_stats; CAPACITY also if n_cells > capacity */
+    fuseflow_stats stats;
+} fuseflow_completion;
+
+/* Creates a server on the current device that may hold at most hbm_budget_bytes of
+ * device memory for its rigs' slots (> 0).  Returns INVALID_ARG, OUT_OF_MEMORY. */
+int fuseflow_server_create(int64_t hbm_budget_bytes, fuseflow_server **out);
+
+/* Adds a rig (as fuseflow_create) with n_slots >= 1 frame slots; *rig_id receives its id.
+ * Returns CAPACITY, with nothing allocated, if the slots would exceed the budget. */
+int fuseflow_server_add_rig(fuseflow_server *srv, const fuseflow_intrinsics *intr,
+                            const fuseflow_extrinsics *extr, int32_t n_cams,
+                            const fuseflow_params *params, int32_t n_slots, int32_t *rig_id);
+
+/* Submits one frame of rig `rig`: depth[i], conf[i], rgb[i] are HOST pointers (pinned
+ * for asynchronous copies) and *out the host output arrays; all stay valid and untouched
+ * until the frame is reported complete.  Never blocks on the device.  *request receives
+ * the frame's id.  Returns INVALID_ARG, CUDA. */
+int fuseflow_server_submit(fuseflow_server *srv, int32_t rig, const void *const *depth,
+                           const float *const *conf, const uint8_t *const *rgb,
+                           const fuseflow_host_cloud *out, int64_t *request);
+
+/* Non-blocking: reports up to max_done finished frames (in completion order) in done[],
+ * their number in *n_done, and starts waiting frames on the slots that became free. */
+int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_t max_done,
+                         int32_t *n_done);
+
+/* Frames submitted but not yet reported by fuseflow_server_poll. */
+int64_t fuseflow_server_pending(const fuseflow_server *srv);
+
+/* Device bytes held by the server's slots (<= the budget). */
+int64_t fuseflow_server_device_bytes(const fuseflow_server *srv);
+
+/* Waits for every slot's stream and releases all resources (NULL is a no-op). */
+void fuseflow_server_destroy(fuseflow_server *srv);
+
 /* Static description of a status code. */
 const char *fuseflow_status_string(int status);
 

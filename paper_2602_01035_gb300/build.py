@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfuseflow.so")
-SOURCES = ["ff_kernels.cu", "ff_api.cu"]
+SOURCES = ["ff_kernels.cu", "ff_api.cu", "ff_server.cu"]
 HEADERS = ["ff_device.cuh", "ff_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

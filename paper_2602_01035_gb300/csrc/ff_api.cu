@@ -488,11 +488,7 @@ int fuseflow_read_stats(fuseflow_ctx* ctx, fuseflow_stats* host_stats, void* str
   if (cudaMemcpyAsync(host_stats, ctx->out.stats, sizeof(fuseflow_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return FUSEFLOW_ERR_CUDA;
-  const unsigned err = (unsigned)host_stats->error;
-  if (err & (kErrSlots | kErrCoarseFull | kErrCells)) return FUSEFLOW_ERR_CAPACITY;
-  if (err & kErrPartials) return FUSEFLOW_ERR_CAPACITY;
-  if (err & (kErrCoarseMiss | kErrList)) return FUSEFLOW_ERR_INTERNAL;
-  return FUSEFLOW_OK;
+  return ffl::status_of_error((unsigned)host_stats->error);
 }
 
 int fuseflow_fuse_frame_host(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,

@@ -76,6 +76,31 @@ cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cu
 
 // Host-side construction of the assign step's tile index and per-camera block constants
 // (caller-sized array of rig.n_cams entries) from the rig constants.
+// Host-mapped output arrays of one served frame (device-accessible addresses of pinned
+// host memory) and the pinned statistics record the copy-out kernel fills.
+struct HostOutDev {
+  float* pos;
+  float* rgb;
+  float* weight;
+  uint32_t* count;
+  uint32_t* rep;
+  unsigned long long* key;
+  long long capacity;
+  fuseflow_stats* stats;
+};
+
+// Copies the first min(n_cells, capacity) cells of a fused cloud and its statistics into
+// host-mapped memory, asynchronously on s (one kernel, coalesced 4-byte stores).
+cudaError_t launch_copyout(const fuseflow_cloud& src, const HostOutDev& dst, cudaStream_t s);
+
+// Status of a frame from its device error bits: capacity overflows first, then internal
+// consistency failures.
+inline int status_of_error(unsigned err) {
+  if (err & (kErrSlots | kErrCoarseFull | kErrCells | kErrPartials)) return FUSEFLOW_ERR_CAPACITY;
+  if (err & (kErrCoarseMiss | kErrList)) return FUSEFLOW_ERR_INTERNAL;
+  return FUSEFLOW_OK;
+}
+
 int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
 int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);

@@ -1113,6 +1113,30 @@ __global__ void __launch_bounds__(kThreads) k_emit(Tables t, OutDev out) {
   }
 }
 
+// Served frames: the cloud's first n cells (n = min(n_cells, capacity)) and the
+// statistics, written into pinned host memory through its mapped addresses.
+__global__ void __launch_bounds__(kThreads) k_copyout(fuseflow_cloud src, HostOutDev dst) {
+  const long long nc = src.stats->n_cells;
+  const long long n = nc < dst.capacity ? nc : dst.capacity;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst.stats = *src.stats;
+  // word ranges of the six arrays, back to back: pos 3n, rgb 3n, weight n, count n,
+  // rep n, key 2n
+  const long long total = 11 * n;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    long long o = w;
+    const uint32_t* from;
+    uint32_t* to;
+    if (o < 3 * n) { from = reinterpret_cast<const uint32_t*>(src.pos); to = reinterpret_cast<uint32_t*>(dst.pos); }
+    else if ((o -= 3 * n) < 3 * n) { from = reinterpret_cast<const uint32_t*>(src.rgb); to = reinterpret_cast<uint32_t*>(dst.rgb); }
+    else if ((o -= 3 * n) < n) { from = reinterpret_cast<const uint32_t*>(src.weight); to = reinterpret_cast<uint32_t*>(dst.weight); }
+    else if ((o -= n) < n) { from = src.count; to = dst.count; }
+    else if ((o -= n) < n) { from = src.rep; to = dst.rep; }
+    else { o -= n; from = reinterpret_cast<const uint32_t*>(src.key); to = reinterpret_cast<uint32_t*>(dst.key); }
+    if (to) to[o] = from[o];
+  }
+}
+
 __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   const unsigned n = max(fcap, ccap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1200,6 +1224,11 @@ void fill_block_consts(const RigDev& rig, BlockConst* out) {
 
 cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cudaStream_t s) {
   k_init_tables<<<1024, 256, 0, s>>>(t, fcap, ccap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copyout(const fuseflow_cloud& src, const HostOutDev& dst, cudaStream_t s) {
+  k_copyout<<<4 * 152, kThreads, 0, s>>>(src, dst);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,275 @@
+// Serving runtime of the FUSE-Flow fusion path: several rigs resident on one GPU, frames
+// from host memory, continuous batching over per-rig frame slots (declared in
+// include/fuseflow.h).  Host code only; the per-frame work is fuseflow_fuse_frame on the
+// slot's own context plus the copy-out kernel.
+#include <algorithm>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "ff_internal.h"
+
+using namespace ffl;
+
+namespace {
+
+struct Request {
+  int64_t id = 0;
+  std::vector<const void*> depth;
+  std::vector<const float*> conf;
+  std::vector<const uint8_t*> rgb;
+  fuseflow_host_cloud out{};
+};
+
+struct Slot {
+  fuseflow_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  char* d_in = nullptr;                 // input staging: per camera depth | conf | rgb
+  fuseflow_stats* h_stats = nullptr;    // pinned, written by the copy-out kernel
+  bool busy = false;
+  int64_t request = 0;
+  int64_t capacity = 0;
+};
+
+struct Rig {
+  int n_cams = 0;
+  size_t depth_bytes = 2;
+  std::vector<size_t> px;               // pixels per camera
+  size_t in_bytes = 0;
+  std::vector<Slot> slots;
+  std::deque<Request> waiting;
+};
+
+size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+void release_slot(Slot& s) {
+  if (s.stream) cudaStreamSynchronize(s.stream);
+  if (s.ctx) fuseflow_destroy(s.ctx);
+  if (s.d_in) cudaFree(s.d_in);
+  if (s.h_stats) cudaFreeHost(s.h_stats);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.stream) cudaStreamDestroy(s.stream);
+  s = Slot{};
+}
+
+}  // namespace
+
+struct fuseflow_server {
+  int device = 0;
+  int64_t budget = 0;
+  int64_t used = 0;
+  int64_t next_id = 1;
+  int64_t pending = 0;
+  std::vector<Rig> rigs;
+};
+
+namespace {
+
+// Host-mapped addresses of the caller's pinned output arrays.
+int map_outputs(const fuseflow_host_cloud& o, fuseflow_stats* h_stats, HostOutDev* d) {
+  auto dev = [](void* p, void** q) {
+    *q = nullptr;
+    if (!p) return true;
+    return cudaHostGetDevicePointer(q, p, 0) == cudaSuccess;
+  };
+  void *a, *b, *c, *e, *f, *g, *h;
+  if (!dev(o.pos, &a) || !dev(o.rgb, &b) || !dev(o.weight, &c) || !dev(o.count, &e) ||
+      !dev(o.rep, &f) || !dev(o.key, &g) || !dev(h_stats, &h)) {
+    cudaGetLastError();
+    return FUSEFLOW_ERR_INVALID_ARG;        // not pinned host memory
+  }
+  d->pos = static_cast<float*>(a);
+  d->rgb = static_cast<float*>(b);
+  d->weight = static_cast<float*>(c);
+  d->count = static_cast<uint32_t*>(e);
+  d->rep = static_cast<uint32_t*>(f);
+  d->key = static_cast<unsigned long long*>(g);
+  d->capacity = o.capacity;
+  d->stats = static_cast<fuseflow_stats*>(h);
+  return FUSEFLOW_OK;
+}
+
+// Enqueues request r on free slot s of rig g: host-to-device copies of the images, the
+// fusion kernels, the copy-out into the caller's host arrays, then the slot's event.
+int start(Rig& g, Slot& s, const Request& r) {
+  HostOutDev hd{};
+  int st = map_outputs(r.out, s.h_stats, &hd);
+  if (st != FUSEFLOW_OK) return st;
+  std::vector<const void*> dp(g.n_cams);
+  std::vector<const float*> cp(g.n_cams);
+  std::vector<const uint8_t*> rp(g.n_cams);
+  size_t o = 0;
+  for (int i = 0; i < g.n_cams; ++i) {
+    const size_t px = g.px[i];
+    char* d = s.d_in + o; o += round256(px * g.depth_bytes);
+    char* c = s.d_in + o; o += round256(px * 4);
+    char* b = s.d_in + o; o += round256(px * 3);
+    if (cudaMemcpyAsync(d, r.depth[i], px * g.depth_bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+        cudaMemcpyAsync(c, r.conf[i], px * 4, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+        cudaMemcpyAsync(b, r.rgb[i], px * 3, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+    dp[i] = d;
+    cp[i] = reinterpret_cast<const float*>(c);
+    rp[i] = reinterpret_cast<const uint8_t*>(b);
+  }
+  fuseflow_cloud cl;
+  st = fuseflow_fuse_frame(s.ctx, dp.data(), cp.data(), rp.data(), &cl, s.stream);
+  if (st != FUSEFLOW_OK) return st;
+  if (launch_copyout(cl, hd, s.stream) != cudaSuccess ||
+      cudaEventRecord(s.done, s.stream) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+  s.busy = true;
+  s.request = r.id;
+  s.capacity = r.out.capacity;
+  return FUSEFLOW_OK;
+}
+
+int status_of(const fuseflow_stats& st, int64_t capacity) {
+  const int s = status_of_error((unsigned)st.error);
+  if (s != FUSEFLOW_OK) return s;
+  return st.n_cells > capacity ? FUSEFLOW_ERR_CAPACITY : FUSEFLOW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fuseflow_server_create(int64_t hbm_budget_bytes, fuseflow_server** out) {
+  if (!out || hbm_budget_bytes <= 0) return FUSEFLOW_ERR_INVALID_ARG;
+  *out = nullptr;
+  fuseflow_server* srv = new (std::nothrow) fuseflow_server();
+  if (!srv) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  if (cudaGetDevice(&srv->device) != cudaSuccess) { delete srv; return FUSEFLOW_ERR_CUDA; }
+  srv->budget = hbm_budget_bytes;
+  *out = srv;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_server_add_rig(fuseflow_server* srv, const fuseflow_intrinsics* intr,
+                            const fuseflow_extrinsics* extr, int32_t n_cams,
+                            const fuseflow_params* params, int32_t n_slots, int32_t* rig_id) {
+  if (!srv || !intr || !extr || !params || !rig_id || n_slots < 1 || n_cams < 1)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  Rig g;
+  g.n_cams = n_cams;
+  g.depth_bytes = params->depth_format == FUSEFLOW_DEPTH_F32 ? 4 : 2;
+  for (int i = 0; i < n_cams; ++i) {
+    if (intr[i].width <= 0 || intr[i].height <= 0) return FUSEFLOW_ERR_INVALID_ARG;
+    const size_t px = (size_t)intr[i].width * intr[i].height;
+    g.px.push_back(px);
+    g.in_bytes += round256(px * g.depth_bytes) + round256(px * 4) + round256(px * 3);
+  }
+  int64_t added = 0;
+  int st = FUSEFLOW_OK;
+  for (int k = 0; k < n_slots && st == FUSEFLOW_OK; ++k) {
+    Slot s;
+    st = fuseflow_create(intr, extr, n_cams, params, &s.ctx);
+    if (st != FUSEFLOW_OK) break;
+    const int64_t bytes = fuseflow_device_bytes(s.ctx) + (int64_t)g.in_bytes;
+    if (srv->used + added + bytes > srv->budget) {
+      fuseflow_destroy(s.ctx);
+      st = FUSEFLOW_ERR_CAPACITY;
+      break;
+    }
+    if (cudaMalloc(&s.d_in, g.in_bytes) != cudaSuccess) {
+      s.d_in = nullptr;
+      release_slot(s);
+      st = FUSEFLOW_ERR_OUT_OF_MEMORY;
+      break;
+    }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&s.h_stats), sizeof(fuseflow_stats), cudaHostAllocMapped) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release_slot(s);
+      st = FUSEFLOW_ERR_CUDA;
+      break;
+    }
+    added += bytes;
+    g.slots.push_back(s);
+  }
+  if (st != FUSEFLOW_OK) {
+    for (Slot& s : g.slots) release_slot(s);
+    return st;
+  }
+  srv->used += added;
+  srv->rigs.push_back(std::move(g));
+  *rig_id = (int32_t)srv->rigs.size() - 1;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_server_submit(fuseflow_server* srv, int32_t rig, const void* const* depth,
+                           const float* const* conf, const uint8_t* const* rgb,
+                           const fuseflow_host_cloud* out, int64_t* request) {
+  if (!srv || rig < 0 || rig >= (int32_t)srv->rigs.size() || !depth || !conf || !rgb || !out ||
+      !request || out->capacity < 0)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  Rig& g = srv->rigs[rig];
+  Request r;
+  r.id = srv->next_id++;
+  for (int i = 0; i < g.n_cams; ++i) {
+    if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
+    r.depth.push_back(depth[i]);
+    r.conf.push_back(conf[i]);
+    r.rgb.push_back(rgb[i]);
+  }
+  r.out = *out;
+  *request = r.id;
+  for (Slot& s : g.slots) {
+    if (s.busy) continue;
+    const int st = start(g, s, r);
+    if (st == FUSEFLOW_OK) ++srv->pending;
+    return st;
+  }
+  g.waiting.push_back(std::move(r));
+  ++srv->pending;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_server_poll(fuseflow_server* srv, fuseflow_completion* done, int32_t max_done,
+                         int32_t* n_done) {
+  if (!srv || !n_done || (max_done > 0 && !done)) return FUSEFLOW_ERR_INVALID_ARG;
+  *n_done = 0;
+  int status = FUSEFLOW_OK;
+  for (int32_t gi = 0; gi < (int32_t)srv->rigs.size(); ++gi) {
+    Rig& g = srv->rigs[gi];
+    for (Slot& s : g.slots) {
+      if (!s.busy || *n_done >= max_done) continue;
+      const cudaError_t q = cudaEventQuery(s.done);
+      if (q == cudaErrorNotReady) continue;
+      fuseflow_completion& c = done[(*n_done)++];
+      c.request = s.request;
+      c.rig = gi;
+      c.stats = *s.h_stats;
+      c.status = q == cudaSuccess ? status_of(c.stats, s.capacity) : FUSEFLOW_ERR_CUDA;
+      if (q != cudaSuccess) cudaGetLastError();
+      s.busy = false;
+      --srv->pending;
+      // continuous batching: the slot takes the rig's oldest waiting frame at once
+      if (!g.waiting.empty()) {
+        Request r = std::move(g.waiting.front());
+        g.waiting.pop_front();
+        const int st = start(g, s, r);
+        if (st != FUSEFLOW_OK) {
+          status = st;
+          --srv->pending;                  // dropped: reported through the return value
+        }
+      }
+    }
+  }
+  return status;
+}
+
+int64_t fuseflow_server_pending(const fuseflow_server* srv) { return srv ? srv->pending : 0; }
+
+int64_t fuseflow_server_device_bytes(const fuseflow_server* srv) { return srv ? srv->used : 0; }
+
+void fuseflow_server_destroy(fuseflow_server* srv) {
+  if (!srv) return;
+  for (Rig& g : srv->rigs)
+    for (Slot& s : g.slots) release_slot(s);
+  delete srv;
+}
+
+}  // extern "C"

@@ -66,6 +66,17 @@ class fuseflow_trace(C.Structure):
                 ("nview", C.c_void_p), ("key", C.c_void_p)]
 
 
+class fuseflow_host_cloud(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("rgb", C.c_void_p), ("weight", C.c_void_p),
+                ("count", C.c_void_p), ("rep", C.c_void_p), ("key", C.c_void_p),
+                ("capacity", C.c_int64)]
+
+
+class fuseflow_completion(C.Structure):
+    _fields_ = [("request", C.c_int64), ("rig", C.c_int32), ("status", C.c_int32),
+                ("stats", fuseflow_stats)]
+
+
 EXPORTS = {
     "fuseflow_default_params": (None, [C.POINTER(fuseflow_params)]),
     "fuseflow_create": (C.c_int, [C.POINTER(fuseflow_intrinsics), C.POINTER(fuseflow_extrinsics),
@@ -93,6 +104,19 @@ EXPORTS = {
                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fuseflow_server_create": (C.c_int, [C.c_int64, C.POINTER(C.c_void_p)]),
+    "fuseflow_server_add_rig": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_intrinsics),
+                                          C.POINTER(fuseflow_extrinsics), C.c_int32,
+                                          C.POINTER(fuseflow_params), C.c_int32,
+                                          C.POINTER(C.c_int32)]),
+    "fuseflow_server_submit": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                         C.POINTER(fuseflow_host_cloud), C.POINTER(C.c_int64)]),
+    "fuseflow_server_poll": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_completion), C.c_int32,
+                                       C.POINTER(C.c_int32)]),
+    "fuseflow_server_pending": (C.c_int64, [C.c_void_p]),
+    "fuseflow_server_device_bytes": (C.c_int64, [C.c_void_p]),
+    "fuseflow_server_destroy": (None, [C.c_void_p]),
 }
 FUSEFLOW_N_STAGES = 6
 
@@ -256,6 +280,50 @@ def fuseflow_stage_name(stage: int) -> str:
 
 def fuseflow_status_string(status: int) -> str:
     return load().fuseflow_status_string(status).decode()
+
+
+def fuseflow_server_create(hbm_budget_bytes: int) -> C.c_void_p:
+    srv = C.c_void_p()
+    _check(load().fuseflow_server_create(int(hbm_budget_bytes), C.byref(srv)),
+           "fuseflow_server_create")
+    return srv
+
+
+def fuseflow_server_add_rig(srv, intr, extr, n_cams: int, params: fuseflow_params,
+                            n_slots: int):
+    """(status, rig id); CAPACITY when the slots would exceed the budget."""
+    rid = C.c_int32(-1)
+    status = load().fuseflow_server_add_rig(srv, intr, extr, n_cams, C.byref(params), n_slots,
+                                            C.byref(rid))
+    return status, rid.value
+
+
+def fuseflow_server_submit(srv, rig: int, depth_ptrs, conf_ptrs, rgb_ptrs,
+                           out: fuseflow_host_cloud) -> int:
+    req = C.c_int64()
+    _check(load().fuseflow_server_submit(srv, rig, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                         _ptr_array(rgb_ptrs), C.byref(out), C.byref(req)),
+           "fuseflow_server_submit")
+    return req.value
+
+
+def fuseflow_server_poll(srv, buf, max_done: int):
+    """Number of completions written into ``buf`` (a fuseflow_completion array)."""
+    n = C.c_int32()
+    _check(load().fuseflow_server_poll(srv, buf, max_done, C.byref(n)), "fuseflow_server_poll")
+    return n.value
+
+
+def fuseflow_server_pending(srv) -> int:
+    return int(load().fuseflow_server_pending(srv))
+
+
+def fuseflow_server_device_bytes(srv) -> int:
+    return int(load().fuseflow_server_device_bytes(srv))
+
+
+def fuseflow_server_destroy(srv) -> None:
+    load().fuseflow_server_destroy(srv)
 
 
 # --------------------------------------------------------------------------- torch helpers

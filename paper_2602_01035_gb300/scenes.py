@@ -40,7 +40,7 @@ import numpy as np
 __all__ = [
     "Camera", "Rig", "Frame", "Plane", "Sphere", "Box", "Room",
     "look_at", "ring_rig", "render_frame", "config1", "config2", "config3", "config4",
-    "serving_rigs", "tiny_rig", "random_frame",
+    "serving_rigs", "serving_frame", "tiny_rig", "random_frame",
 ]
 
 
@@ -479,6 +479,14 @@ def serving_rigs(n_rigs=12, seed=5999):
     rng2 = np.random.default_rng(seed + 1)
     prims = [Plane((0, 0, 1), 0.0)] + _ground_objects(rng2, 10, 0.0, 2.0, 0.2, 0.8)
     return rigs, prims
+
+
+def serving_frame(index: int, n_rigs: int = 12, seed: int = 5999) -> Frame:
+    """Frame 0 of serving rig `index` (noise seed 1000*5 + index); a module-level function so
+    that a process pool can render the rigs in parallel."""
+    rigs, prims = serving_rigs(n_rigs, seed)
+    return render_frame(rigs[index], prims, seed=1000 * 5 + index, noise_k=0.0015,
+                        flying_frac=0.01)
 
 
 # ----------------------------------------------------------------------------- tiny cases

@@ -110,3 +110,22 @@ def test_header_has_no_torch_types():
     text = open(HEADER).read()
     assert "torch" not in text.lower().replace("pytorch", "") or "at::" not in text
     assert "at::Tensor" not in text and "c10" not in text
+
+
+def test_server_rejects_bad_arguments_without_a_gpu(ffmod):
+    lib = ffmod.load()
+    srv = C.c_void_p()
+    assert lib.fuseflow_server_create(0, C.byref(srv)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_server_create(-5, C.byref(srv)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    n = C.c_int32(7)
+    assert lib.fuseflow_server_poll(None, None, 0, C.byref(n)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    rid = C.c_int32()
+    p = ffmod.fuseflow_default_params()
+    assert lib.fuseflow_server_add_rig(None, None, None, 1, C.byref(p), 1,
+                                       C.byref(rid)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    req = C.c_int64()
+    assert lib.fuseflow_server_submit(None, 0, None, None, None, None,
+                                      C.byref(req)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_server_pending(None) == 0
+    assert lib.fuseflow_server_device_bytes(None) == 0
+    lib.fuseflow_server_destroy(None)

@@ -1,0 +1,131 @@
+"""The serving runtime (fuseflow_server_*): results alone and in a mix, budget admission,
+continuous batching over slots.  Frames come from pinned host memory and results land in
+pinned host arrays; every comparison is bitwise against the plain device path, whose
+parity with the oracle is checked in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+from paper_2602_01035_gb300 import scenes as S
+from parity import run_gpu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_01035_gb300 import fuseflow, serving
+    fuseflow.load()
+    return fuseflow, serving
+
+
+def _cases():
+    r1, _, f1 = S.config1()
+    r2 = S.tiny_rig(n=3, width=96, height=64, spread_deg=25.0, fx=80.0, fy=78.0)
+    f2 = S.random_frame(r2, seed=21, zero_frac=0.02, flying_frac=0.01)
+    r3 = S.tiny_rig(n=5, width=64, height=48, depth_format="f32", depth_scale=1.0, spread_deg=20.0)
+    f3 = S.random_frame(r3, seed=22, zero_frac=0.05)
+    return [(r1, f1), (r2, f2), (r3, f3)]
+
+
+def _alone(F, rig, fr):
+    ff = F.FuseFlow(rig)
+    try:
+        out = run_gpu(ff, fr, torch, with_trace=False)
+    finally:
+        ff.close()
+    return out
+
+
+def _same(a: dict, b: dict):
+    for k in ("pos", "rgb", "weight", "count", "rep", "key"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_results_alone_and_in_the_mix(mods):
+    F, SV = mods
+    cases = _cases()
+    alone = [_alone(F, r, f) for r, f in cases]
+    srv = SV.Server(8 << 30)
+    try:
+        rids = [srv.add_rig(r, n_slots=2) for r, _ in cases]
+        frames = [SV.pinned_frame(f) for _, f in cases]
+        # every rig three times, interleaved, all in flight at once: more frames than slots
+        order = [0, 1, 2, 2, 1, 0, 1, 2, 0]
+        bufs, reqs = {}, {}
+        for k, r in enumerate(order):
+            hc = SV.HostCloud(srv.rigs[r]["capacity"])
+            req = srv.submit(rids[r], frames[r], hc)
+            bufs[req] = (r, hc)
+        done = srv.drain()
+        assert len(done) == len(order) and srv.pending() == 0
+        for req, rig, status, st in done:
+            r, hc = bufs[req]
+            assert rig == rids[r] and status == F.FUSEFLOW_OK
+            assert st["n_cells"] == alone[r]["stats"]["n_cells"]
+            _same(hc.cells(st["n_cells"]), alone[r]["cells"])
+    finally:
+        srv.close()
+
+
+def test_budget_admission(mods):
+    F, SV = mods
+    (r1, f1), (r2, _), _ = _cases()
+    srv = SV.Server(1 << 30)
+    try:
+        rid = srv.add_rig(r1, n_slots=1)
+        used = srv.device_bytes()
+        assert 0 < used <= 1 << 30
+        # a rig whose slots do not fit is refused and leaves nothing behind
+        status, _ = F.fuseflow_server_add_rig(srv.srv, *F.rig_arrays(r2), len(r2.cameras),
+                                              F.fuseflow_default_params(), 100000)
+        assert status == F.FUSEFLOW_ERR_CAPACITY
+        assert srv.device_bytes() == used
+        hc = SV.HostCloud(srv.rigs[rid]["capacity"])
+        pf = SV.pinned_frame(f1)                # inputs stay alive until completion
+        srv.submit(rid, pf, hc)
+        (req, rig, status, st), = srv.drain()
+        assert status == F.FUSEFLOW_OK and st["n_cells"] > 0
+    finally:
+        srv.close()
+
+
+def test_one_slot_serves_a_queue_in_order(mods):
+    F, SV = mods
+    r2 = S.tiny_rig(n=2, width=64, height=48)
+    frs = [S.random_frame(r2, seed=30 + k) for k in range(5)]
+    alone = [_alone(F, r2, f) for f in frs]
+    srv = SV.Server(2 << 30)
+    try:
+        rid = srv.add_rig(r2, n_slots=1)
+        bufs = {}
+        pinned = [SV.pinned_frame(f) for f in frs]   # alive until every frame completes
+        for k in range(len(frs)):
+            hc = SV.HostCloud(srv.rigs[rid]["capacity"])
+            bufs[srv.submit(rid, pinned[k], hc)] = (k, hc)
+        assert srv.pending() == 5
+        done = srv.drain()
+        assert [d[0] for d in done] == sorted(bufs)            # FIFO on the single slot
+        for req, _, status, st in done:
+            k, hc = bufs[req]
+            assert status == F.FUSEFLOW_OK
+            _same(hc.cells(st["n_cells"]), alone[k]["cells"])
+    finally:
+        srv.close()
+
+
+def test_capacity_of_the_host_arrays_is_reported(mods):
+    F, SV = mods
+    r1, _, f1 = S.config1()
+    srv = SV.Server(1 << 30)
+    try:
+        rid = srv.add_rig(r1, n_slots=1)
+        hc = SV.HostCloud(10)
+        pf = SV.pinned_frame(f1)
+        srv.submit(rid, pf, hc)
+        (_, _, status, st), = srv.drain()
+        assert status == F.FUSEFLOW_ERR_CAPACITY and st["n_cells"] > 10
+    finally:
+        srv.close()
