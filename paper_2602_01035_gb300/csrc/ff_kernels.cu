@@ -272,11 +272,18 @@ __device__ __forceinline__ void load8(const DT* __restrict__ d, const float* __r
   }
 }
 
-// Adds n points to coarse key k: the block table first, the global table after 64 probes.
+// Adds n points to coarse key k: the block table while it is at most 3/4 full (so that
+// probe runs stay short), else, or after 32 probes, the global table directly.
 template <int TS>
 __device__ __forceinline__ void count_add(const Tables& t, unsigned long long* s_key,
-                                          unsigned* s_cnt, unsigned long long k, unsigned n) {
-  const int h = local_pos<TS>(s_key, kKeyEmpty, k, 64);
+                                          unsigned* s_cnt, unsigned* s_fill,
+                                          unsigned long long k, unsigned n) {
+  int h = -1;
+  if (*static_cast<volatile unsigned*>(s_fill) < 3u * TS / 4u) {
+    bool fresh;
+    h = local_pos<TS>(s_key, kKeyEmpty, k, 32, fresh);
+    if (fresh) atomicAdd(s_fill, 1u);
+  }
   if (h >= 0) {
     atomicAdd(&s_cnt[h], n);
   } else {
@@ -292,6 +299,7 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   constexpr int TS = 2048;                                      // block table of coarse keys
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
+  __shared__ unsigned s_fill;                                    // keys in the block table
   __shared__ unsigned s_red[kThreads / 32][9];
   const RigDev& rig = *rigp;
   const int cam = blockIdx.y;
@@ -305,6 +313,7 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   const long long c0 = (long long)blockIdx.x * chunks;          // first chunk of 2048 pixels
   const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
+  if (threadIdx.x == 0) s_fill = 0u;
   __syncthreads();
 
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
@@ -335,48 +344,68 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     unsigned nhead = 0u, run = 0u, nruns = 0u;
     int cx = 0, cy = 0, cz = 0;
     if (pc < npx) {
-      int xx = x, yy = y;
-      float ry = __ldg(&rays[C.ray_y + min(yy, C.H - 1)].x);
+      // the pixels' ray components: one row and 16-byte aligned rays (every rig whose
+      // widths are multiples of 8) take four vector loads, other groups one load per pixel
+      float rxk[kCountPx], ryk[kCountPx];
+      if (x + kCountPx <= C.W && ((C.ray_x + x) & 1) == 0) {
+        const float4* r4 = reinterpret_cast<const float4*>(rays + C.ray_x + x);
+#pragma unroll
+        for (int k = 0; k < kCountPx / 2; ++k) {
+          const float4 v = __ldg(r4 + k);
+          rxk[2 * k] = v.x;
+          rxk[2 * k + 1] = v.z;
+        }
+        const float ry = __ldg(&rays[C.ray_y + y].x);
+#pragma unroll
+        for (int k = 0; k < kCountPx; ++k) ryk[k] = ry;
+      } else {
+        int xx = x, yy = y;
+#pragma unroll
+        for (int k = 0; k < kCountPx; ++k) {
+          rxk[k] = __ldg(&rays[C.ray_x + xx].x);
+          ryk[k] = __ldg(&rays[C.ray_y + min(yy, C.H - 1)].x);
+          if (++xx == C.W) { xx = 0; ++yy; }
+        }
+      }
+      // branch-free per pixel: every lane evaluates every pixel, predicates select
 #pragma unroll
       for (int k = 0; k < kCountPx; ++k) {
-        if (pc + k < npx && Depth<DT>::valid(dcur[k])) {
-          ++nv;
-          if (!use_conf || ccur[k] > tau) {                       // Eq. 9
-            ++ng;
-            float P[3];
-            world_point(C, Depth<DT>::z(dcur[k]), __ldg(&rays[C.ray_x + xx].x), ry, P);
+        const bool valid = pc + k < npx && Depth<DT>::valid(dcur[k]);
+        const bool gated = valid && (!use_conf || ccur[k] > tau);  // Eq. 9
+        nv += valid ? 1u : 0u;
+        ng += gated ? 1u : 0u;
+        float P[3];
+        world_point(C, valid ? Depth<DT>::z(dcur[k]) : 0.0f, rxk[k], ryk[k], P);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { fmn[a] = fminf(fmn[a], P[a]); fmx[a] = fmaxf(fmx[a], P[a]); }
-            // coarse coordinates floor(P / s0); the finest index floor(r 2^Lmax) is in
-            // [-2^19, 2^19) exactly when floor(r) is in [-2^(19-Lmax), 2^(19-Lmax))
-            const int ix = (int)floorf(__fmul_rn(P[0], inv_s0u));
-            const int iy = (int)floorf(__fmul_rn(P[1], inv_s0u));
-            const int iz = (int)floorf(__fmul_rn(P[2], inv_s0u));
-            if (ix >= -lim && ix < lim && iy >= -lim && iy < lim && iz >= -lim && iz < lim) {
-              if (run && ix == cx && iy == cy && iz == cz) {
-                ++run;
-              } else {
-                if (run) {                                        // a run ends
-                  if (nruns == 1u) {
-                    khead = pack_key(0, cx, cy, cz);
-                    nhead = run;
-                  } else {
-                    count_add<TS>(t, s_key, s_cnt, pack_key(0, cx, cy, cz), run);
-                  }
-                }
-                cx = ix; cy = iy; cz = iz;
-                run = 1u;
-                ++nruns;
-              }
-            } else {
-              ++noor;
-            }
+        for (int a = 0; a < 3; ++a) {
+          fmn[a] = gated ? fminf(fmn[a], P[a]) : fmn[a];
+          fmx[a] = gated ? fmaxf(fmx[a], P[a]) : fmx[a];
+        }
+        // coarse coordinates floor(P / s0); the finest index floor(r 2^Lmax) is in
+        // [-2^19, 2^19) exactly when floor(r) is in [-2^(19-Lmax), 2^(19-Lmax))
+        const int ix = (int)floorf(__fmul_rn(P[0], inv_s0u));
+        const int iy = (int)floorf(__fmul_rn(P[1], inv_s0u));
+        const int iz = (int)floorf(__fmul_rn(P[2], inv_s0u));
+        const bool inr = (unsigned)(ix + lim) < (unsigned)(2 * lim) &&
+                         (unsigned)(iy + lim) < (unsigned)(2 * lim) &&
+                         (unsigned)(iz + lim) < (unsigned)(2 * lim);
+        noor += (gated && !inr) ? 1u : 0u;
+        const bool counted = gated && inr;
+        const bool same = run && ix == cx && iy == cy && iz == cz;
+        if (counted && !same && run) {                            // a run ends
+          if (nruns == 1u) {
+            khead = pack_key(0, cx, cy, cz);
+            nhead = run;
+          } else {
+            count_add<TS>(t, s_key, s_cnt, &s_fill, pack_key(0, cx, cy, cz), run);
           }
         }
-        if (++xx == C.W) {
-          xx = 0;
-          ++yy;
-          ry = __ldg(&rays[C.ray_y + min(yy, C.H - 1)].x);
+        if (counted) {
+          run = same ? run + 1u : 1u;
+          nruns += same ? 0u : 1u;
+          cx = ix;
+          cy = iy;
+          cz = iz;
         }
       }
     }
@@ -401,8 +430,8 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
           start = start || f2;
         }
       }
-      if (nruns >= 2u && !cont) count_add<TS>(t, s_key, s_cnt, khead, nhead);
-      if (ktail != kKeyEmpty && (lane == 31 || nstart)) count_add<TS>(t, s_key, s_cnt, ktail, v);
+      if (nruns >= 2u && !cont) count_add<TS>(t, s_key, s_cnt, &s_fill, khead, nhead);
+      if (ktail != kKeyEmpty && (lane == 31 || nstart)) count_add<TS>(t, s_key, s_cnt, &s_fill, ktail, v);
     }
     x += kCountBlockPx;                                           // next chunk's first pixel
     while (x >= C.W) { x -= C.W; ++y; }
