@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--frames-per-step", type=int, default=300)
     ap.add_argument("--pool", type=int, default=8, help="distinct frames cycled (> L2 in total)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-frames", type=int, default=64)
+    ap.add_argument("--e2e-frames", type=int, default=256)
     ap.add_argument("--slots", type=int, default=4,
                     help="frames in flight on separate streams for the batched line")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
@@ -357,43 +357,59 @@ def run_ours(args, rank, world, local_rank):
                  "frac": round(path_bytes / (ms / 1e3 / (args.steps * FPS)) / 1e9 / peak, 4)}
 
     # ------------------------------------------------------------ end to end (host buffers)
-    e2e = None
-    n_e2e = min(args.e2e_frames, FPS)
-    pinned = []
-    for fr in pool:
-        d = [torch.from_numpy(x).pin_memory() for x in fr.depth]
-        c = [torch.from_numpy(x).pin_memory() for x in fr.conf]
-        r = [torch.from_numpy(x).pin_memory() for x in fr.rgb]
-        pinned.append((d, c, r))
+    # The public serving API on this rig: frames from pinned host memory, results into
+    # pinned host arrays, `slots` frames in flight (copies overlap other frames' kernels).
+    from collections import deque
+    from paper_2602_01035_gb300 import serving as SV
+    n_e2e = max(1, min(args.e2e_frames, FPS))
+    B = max(1, args.slots)
+    pinned = [SV.pinned_frame(fr) for fr in pool]
     cap = ff.capacity
-    outs = [torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
-            torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
-            torch.empty(cap, dtype=torch.float32).pin_memory(),
-            torch.empty(cap, dtype=torch.int32).pin_memory(),
-            torch.empty(cap, dtype=torch.int32).pin_memory(),
-            torch.empty(cap, dtype=torch.int64).pin_memory()]
-    optr = [o.data_ptr() for o in outs]
+    srv = SV.Server(1 << 40)
+    rid = srv.add_rig(rig, n_slots=B)
+    outs = deque(SV.HostCloud(cap) for _ in range(B + 1))
 
-    def host_frame(i):
-        d, c, r = pinned[i % len(pinned)]
-        return F.fuseflow_fuse_frame_host(ff.ctx, [t.data_ptr() for t in d], [t.data_ptr() for t in c],
-                                          [t.data_ptr() for t in r], *optr, sh)
+    def serve(n_frames):
+        sent, got, d2h_bytes, flying = 0, 0, 0, {}
+        while got < n_frames:
+            while sent < n_frames and outs:
+                buf = outs.popleft()
+                flying[srv.submit(rid, pinned[sent % len(pinned)], buf)] = buf
+                sent += 1
+            for req, _, status, st_ in srv.poll():
+                outs.append(flying.pop(req))
+                d2h_bytes += st_["n_cells"] * CELL_OUT_BYTES + 48
+                got += 1
+        return d2h_bytes
 
-    for i in range(3):
-        host_frame(i)
-    d2h = 0
-    torch.cuda.synchronize(dev)
+    serve(2 * B)
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
-    for i in range(n_e2e):
-        s_, st_ = host_frame(i)
-        d2h += st_.n_cells * CELL_OUT_BYTES + 48
-    t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    e2e = {"value": round(n_e2e * px / e2e_s * world, 1), "unit": "px/s",
-           "frames_per_s": round(n_e2e / e2e_s * world, 2),
+    d2h = serve(n_e2e)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev) / 1e3
+    srv.close()
+    e2e = {"value": round(job_rate(n_e2e * px, world, e2e_s * 1e3), 1), "unit": "px/s",
+           "frames_per_s": round(job_rate(n_e2e, world, e2e_s * 1e3), 2),
            "h2d_bytes_per_step": int(frame_bytes * FPS),
            "d2h_bytes_per_step": int(d2h / n_e2e * FPS),
-           "frames_timed": n_e2e, "entry_point": "fuseflow_fuse_frame_host"}
+           "frames_timed": n_e2e, "slots": B,
+           "entry_point": "fuseflow_server_submit / fuseflow_server_poll (host buffers)"}
+    # the synchronous single-call host entry point, for reference
+    ctx_host = [SV.HostCloud(cap)]
+    h = ctx_host[0].c
+    t0 = time.perf_counter()
+    n_single = min(16, n_e2e)
+    for i in range(n_single):
+        fr = pinned[i % len(pinned)]
+        F.fuseflow_fuse_frame_host(ff.ctx, fr["depth"], fr["conf"], fr["rgb"], h.pos, h.rgb,
+                                   h.weight, h.count, h.rep, h.key, sh)
+    e2e["single_call_frames_per_s"] = round(n_single / (time.perf_counter() - t0), 2)
+
+    # ------------------------------------------------------------ the other configurations
+    configs = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        configs = run_configs(dev)
 
     # ------------------------------------------------------------ served vs plain
     serving = None
@@ -404,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rig, pool[:8])
+        cpu["all_cores"] = cpu_baseline_all_cores(rig, pool[:8])
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "px/s", "n_gpus": world,
@@ -422,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "path_roofline": path_roof,
         "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "stage_roofline": stages,
-        "batched": batched, "serving": serving,
+        "batched": batched, "serving": serving, "other_configs": configs,
         "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
         "cells_per_frame": int(n_cells), "status_ok": ok_status,
         "clocks": clocks, "cpu_baseline": cpu,
@@ -432,6 +449,55 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- other configs
+def run_configs(dev, frames_each: int = 64):
+    """Device-resident throughput of the other rigs on the plain path (one frame per fuse
+    call, CUDA events on the launching stream): 2x160x120 float32, 4x640x480, and the
+    2/8/16/32-camera 1024x1024 rig-scaling sweep."""
+    import multiprocessing as mp
+    import torch
+    from paper_2602_01035_gb300 import fuseflow as F
+    from paper_2602_01035_gb300 import scenes as S
+
+    specs = [("cfg1",), ("cfg2", 0), ("cfg2", 1), ("cfg4", 2), ("cfg4", 8), ("cfg4", 16), ("cfg4", 32)]
+    with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
+        rendered = pool.map(S.config_frame, specs)
+    groups = {}
+    for spec, (rig, fr) in zip(specs, rendered):
+        key = spec[0] if spec[0] != "cfg4" else f"cfg4_{spec[1]}cams"
+        groups.setdefault(key, (rig, []))[1].append(fr)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for key, (rig, frs) in groups.items():
+        dev_frames = []
+        for fr in frs:
+            d = [torch.from_numpy(x).to(dev) for x in fr.depth]
+            c = [torch.from_numpy(x).to(dev) for x in fr.conf]
+            r = [torch.from_numpy(x).to(dev) for x in fr.rgb]
+            dev_frames.append((d, c, r, [t.data_ptr() for t in d], [t.data_ptr() for t in c],
+                               [t.data_ptr() for t in r]))
+        ff = F.FuseFlow(rig)
+        for i in range(4):
+            t = dev_frames[i % len(dev_frames)]
+            F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(frames_each):
+            t = dev_frames[i % len(dev_frames)]
+            F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        status, st = ff.stats(stream.cuda_stream, check=False)
+        px = rig.n_pixels
+        out[key] = {"cams": rig.n_cams, "px_per_frame": px, "frames_per_s": round(frames_each / (ms / 1e3), 2),
+                    "px_per_s": round(frames_each * px / (ms / 1e3), 1),
+                    "px_per_s_per_camera": round(frames_each * px / (ms / 1e3) / rig.n_cams, 1),
+                    "cells": int(st.n_cells), "status_ok": status == F.FUSEFLOW_OK}
+        ff.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- serving
@@ -523,6 +589,29 @@ def cpu_baseline(rig, frames, row_step=1):
     return {"value": round(n / dt, 1), "unit": "px/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(frames)} frame(s) of the 8x1280x720 rig, rows y % {row_step} == 0 "
                       f"back-projected ({n} px), {dt:.1f} s on one host core"}
+
+
+def _oracle_worker(item):
+    rig, fr = item
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.fuse_frame(rig, fr, {}, points=False)
+    return rig.n_pixels, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(rig, frames):
+    """The oracle on every host core at once: one process per core, one frame each."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    items = [(rig, frames[k % len(frames)]) for k in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_worker, items)
+    px = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": round(px / wall, 1), "unit": "px/s", "cores": n, "kind": "oracle",
+            "sample": f"{n} processes, one 8x1280x720 frame each, concurrently; "
+                      f"slowest {wall:.1f} s"}
 
 
 def run_reference(args, rank, world):

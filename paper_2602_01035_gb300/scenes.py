@@ -40,7 +40,7 @@ import numpy as np
 __all__ = [
     "Camera", "Rig", "Frame", "Plane", "Sphere", "Box", "Room",
     "look_at", "ring_rig", "render_frame", "config1", "config2", "config3", "config4",
-    "serving_rigs", "serving_frame", "tiny_rig", "random_frame",
+    "serving_rigs", "serving_frame", "config_frame", "tiny_rig", "random_frame",
 ]
 
 
@@ -479,6 +479,23 @@ def serving_rigs(n_rigs=12, seed=5999):
     rng2 = np.random.default_rng(seed + 1)
     prims = [Plane((0, 0, 1), 0.0)] + _ground_objects(rng2, 10, 0.0, 2.0, 0.2, 0.8)
     return rigs, prims
+
+
+def config_frame(spec) -> tuple:
+    """(rig, frame) of a configuration named by a picklable spec: ("cfg1",), ("cfg2", f),
+    ("cfg3", f) or ("cfg4", n_cams); module-level so that a process pool can render them."""
+    name = spec[0]
+    if name == "cfg1":
+        rig, _, fr = config1()
+    elif name == "cfg2":
+        rig, _, fr = config2(frame=spec[1])
+    elif name == "cfg3":
+        rig, _, fr = config3(frame=spec[1])
+    elif name == "cfg4":
+        rig, _, fr = config4(n_cams=spec[1])
+    else:
+        raise ValueError(name)
+    return rig, fr
 
 
 def serving_frame(index: int, n_rigs: int = 12, seed: int = 5999) -> Frame:
