@@ -331,10 +331,6 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     const long long max_chunks = (max_px + 2047) / 2048;
     ctx->geo.count_blocks_x = (int)((max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
-  int tiles_max = 0;
-  for (int i = 0; i < n_cams; ++i)
-    tiles_max = std::max(tiles_max, ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16));
-  ctx->geo.tiles_max = tiles_max;
   ctx->geo.emit_blocks = std::max(1, sms * 8);
 
   // ---------------------------------------------------------------- device memory
@@ -753,13 +749,11 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   if (!depth || !conf || !rgb || !pos || !rgb_out || !weight || !count || !rep || !key || !stats)
     return FUSEFLOW_ERR_INVALID_ARG;
   long long n_px = 0, max_px = 0, n_rays = 0;
-  int tiles_max = 0;
   for (int i = 0; i < n_cams; ++i) {
     const long long px = (long long)intr[i].width * intr[i].height;
     n_px += px;
     max_px = std::max(max_px, px);
     n_rays += intr[i].width + intr[i].height;
-    tiles_max = std::max(tiles_max, ((intr[i].width + 31) / 32) * ((intr[i].height + 15) / 16));
     if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
   }
   const long long max_cells = params->max_cells > 0 ? params->max_cells : kStaticMaxCells;
@@ -808,7 +802,6 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   geo.depth_f32 = rig.depth_f32;
   geo.count_blocks_x = (int)((max_px + 2047) / 2048);
   geo.count_chunks = 1;
-  geo.tiles_max = tiles_max;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   geo.emit_blocks = std::max(1, sms * 8);

@@ -67,7 +67,6 @@ struct Geometry {
   int depth_f32;
   int count_blocks_x;            // blocks per camera of the coarse-count step (max over cams)
   int count_chunks;              // 1024-pixel chunks per block of the coarse-count step
-  int tiles_max;                 // 32x16 tiles per camera (max over cams)
   int emit_blocks;
   TileIndex tiles;               // assign-step tiles
 };
