@@ -149,6 +149,20 @@ int fuseflow_fuse_frame_host(fuseflow_ctx *ctx, const void *const *depth,
                              uint32_t *rep, uint64_t *key, fuseflow_stats *host_stats,
                              void *stream);
 
+/* Multi-Camera Depth Consistency error of Eq. 12 on a point set, against the rig's depth
+ * maps of one frame: for each point P_k (pos: DEVICE float32 [n_points][3], world metres),
+ * the cameras i that see it (z(T_i P_k) > 0, nearest pixel floor(pi(T_i P_k) + 1/2) inside
+ * the image, valid D_i there, and not hidden behind the observed surface:
+ * z(T_i P_k) <= D_i + occlusion_m; INFINITY disables that test) and the mean over them of
+ * |z(T_i P_k) - D_i(pi(T_i P_k))|.  occlusion_m >= 0 (metres).  err_m (DEVICE float [n], metres, NaN where no camera
+ * sees the point) and n_visible (DEVICE int32 [n]) may be NULL.  *mc_m receives E_MC, the
+ * mean of the per-point errors over the points seen by at least one camera (metres), and
+ * *n_used their number.  depth[i] are DEVICE pointers as for fuseflow_fuse_frame.  Waits
+ * for `stream` before returning.  Returns INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+int fuseflow_mc_error(fuseflow_ctx *ctx, const float *pos, int64_t n_points,
+                      const void *const *depth, double occlusion_m, float *err_m,
+                      int32_t *n_visible, double *mc_m, int64_t *n_used, void *stream);
+
 /* Registers (or, with NULL, clears) a per-pixel trace written by later fuse calls. */
 int fuseflow_set_trace(fuseflow_ctx *ctx, const fuseflow_trace *trace);
 

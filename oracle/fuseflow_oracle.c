@@ -513,3 +513,54 @@ int orc_fuse_frame(const orc_camera *cams, int32_t n, const orc_params *p,
     free(ckeys); free(ccount); free(b_in); free(b_out); free(amb); free(pkey);
     return rc;
 }
+
+/* ---------------------------------------------------------------- Eq. 12 MC error */
+int orc_mc_error(const orc_camera *cams, int32_t n, const orc_params *p,
+                 const void *const *depth, const double *pts, int64_t n_pts,
+                 double occlusion_m, double *err, int32_t *nvis, double *tie_px, double *mc_m,
+                 int64_t *n_used) {
+    if (!cams || n < 1 || !p || !depth || (n_pts > 0 && !pts) || !mc_m || !n_used)
+        return ORC_ERR_ARG;
+    double total = 0.0;
+    int64_t used = 0;
+    for (int64_t k = 0; k < n_pts; ++k) {
+        const double *P = pts + 3 * k;
+        double sum = 0.0, tie = INFINITY;
+        int32_t vis = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const orc_camera *c = &cams[i];
+            double a[3];
+            to_camera(c, P, a);                       /* T_i P_k */
+            if (!(a[2] > 0.0)) continue;              /* behind camera i */
+            const double u = c->fx * a[0] / a[2] + c->cx;   /* pi(T_i P_k) */
+            const double v = c->fy * a[1] / a[2] + c->cy;
+            const double px = floor(u + 0.5), py = floor(v + 0.5);
+            if (px >= -1.0 && py >= -1.0 && px <= c->width && py <= c->height) {
+                /* the pixel decision matters here (inside the image or at its border) */
+                const double fu = u + 0.5 - px, fv = v + 0.5 - py;
+                const double tu = fu < 1.0 - fu ? fu : 1.0 - fu, tv = fv < 1.0 - fv ? fv : 1.0 - fv;
+                if (tu < tie) tie = tu;
+                if (tv < tie) tie = tv;
+            }
+            if (px < 0.0 || py < 0.0 || px >= c->width || py >= c->height) continue;
+            double D;
+            if (!depth_at(depth[i], p->depth_format, (int64_t)py * c->width + (int64_t)px,
+                          p->depth_scale, &D))
+                continue;                             /* no observed depth there */
+            if (a[2] > D + occlusion_m) continue;     /* behind the observed surface: occluded */
+            sum += fabs(a[2] - D);                    /* |z(T_i P_k) - D_i(pi(T_i P_k))| */
+            ++vis;
+        }
+        const double e = vis ? sum / vis : NAN;
+        if (err) err[k] = e;
+        if (nvis) nvis[k] = vis;
+        if (tie_px) tie_px[k] = tie;
+        if (vis) {
+            total += e;
+            ++used;
+        }
+    }
+    *mc_m = used ? total / (double)used : NAN;
+    *n_used = used;
+    return ORC_OK;
+}

@@ -93,6 +93,22 @@ int orc_fuse_frame(const orc_camera *cams, int32_t n_cams, const orc_params *p,
                    const uint8_t *const *rgb, orc_points *pts, orc_cells *cells,
                    int64_t cell_capacity, orc_stats *st);
 
+/* Eq. 12, the Multi-Camera Depth Consistency (MC) error of a point set rho = pts[n_pts][3]
+ * (world frame, metres).  Reading of "visible": camera i is in gamma(P) when P lies in
+ * front of it (z(T_i P) > 0), the nearest pixel floor(pi(T_i P) + 1/2) is inside the image,
+ * D_i there is valid (> 0, finite) and P is not hidden behind the surface camera i
+ * observes: z(T_i P) <= D_i + occlusion_m (INFINITY: no occlusion test).
+ * Points visible in no camera are left out of the outer mean.  Per point (any pointer may
+ * be NULL): err[k] = mean over gamma of |z(T_i P_k) - D_i(pixel)| in metres (NaN when gamma
+ * is empty), nvis[k] = |gamma(P_k)|, tie_px[k] = smallest distance of u + 1/2 or v + 1/2
+ * to an integer over the cameras in front of which P_k projects into the image or onto its
+ * one-pixel border (where the rounding decides).  *mc_m = the mean of err over the points used and
+ * *n_used their number.  Uses p->depth_format and p->depth_scale only. */
+int orc_mc_error(const orc_camera *cams, int32_t n_cams, const orc_params *p,
+                 const void *const *depth, const double *pts, int64_t n_pts,
+                 double occlusion_m, double *err, int32_t *nvis, double *tie_px,
+                 double *mc_m, int64_t *n_used);
+
 #ifdef __cplusplus
 }
 #endif

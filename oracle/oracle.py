@@ -83,6 +83,11 @@ def _load():
         lib.orc_neighbours.restype = C.c_int
         lib.orc_neighbours.argtypes = [C.POINTER(_Camera), C.c_int32, C.c_int32,
                                        C.POINTER(C.c_int32)]
+        lib.orc_mc_error.restype = C.c_int
+        lib.orc_mc_error.argtypes = [C.POINTER(_Camera), C.c_int32, C.POINTER(_Params),
+                                     C.POINTER(C.c_void_p), C.c_void_p, C.c_int64, C.c_double,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int64)]
         lib.orc_default_params.restype = None
         lib.orc_default_params.argtypes = [C.POINTER(_Params)]
         _lib = lib
@@ -175,6 +180,38 @@ def fuse_frame(rig, frame, params: dict | None = None, points: bool = True,
                     for name, _ in _Stats._fields_}
     out["params"] = {name: getattr(prm, name) for name, _ in _Params._fields_}
     return out
+
+
+MC_OCCLUSION_M = 0.05   # about three times the sensor noise at 3 m (0.0015 z^2)
+
+
+def mc_error(rig, depth, points, occlusion_m: float = MC_OCCLUSION_M,
+             depth_format: str | None = None) -> dict:
+    """Eq. 12 on a point set (n x 3 metres) against the rig's depth maps (FP64 oracle):
+    per-point error (metres), visible cameras, tie margin (px), the mean and its count."""
+    lib = _load()
+    prm = _Params()
+    lib.orc_default_params(C.byref(prm))
+    fmt = depth_format or rig.depth_format
+    prm.depth_format = DEPTH_FORMATS[fmt]
+    prm.depth_scale = rig.depth_scale
+    want = {"u16": np.uint16, "f32": np.float32, "f64": np.float64}[fmt]
+    keep = [np.ascontiguousarray(d, dtype=want) for d in depth]
+    dep = (C.c_void_p * rig.n_cams)(*[d.ctypes.data for d in keep])
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    n = len(pts)
+    err = np.zeros(max(n, 1), np.float64)
+    nvis = np.zeros(max(n, 1), np.int32)
+    tie = np.zeros(max(n, 1), np.float64)
+    mc = C.c_double()
+    used = C.c_int64()
+    rc = lib.orc_mc_error(_cams(rig), rig.n_cams, C.byref(prm), dep, pts.ctypes.data, n,
+                          float(occlusion_m), err.ctypes.data, nvis.ctypes.data, tie.ctypes.data, C.byref(mc),
+                          C.byref(used))
+    if rc != 0:
+        raise RuntimeError(f"orc_mc_error failed with status {rc}")
+    return {"err_m": err[:n], "nvis": nvis[:n], "tie_px": tie[:n], "mc_m": mc.value,
+            "n_used": used.value}
 
 
 def key_fields(key):

@@ -42,6 +42,8 @@ struct fuseflow_ctx {
   // staging for the host-buffer entry point
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
+  // per-block sums of the MC error (Eq. 12)
+  void* d_mc = nullptr;
   // stage timing ring
   bool timing = false;
   std::vector<cudaEvent_t> events;     // kTimingRing * (FUSEFLOW_N_STAGES + 1)
@@ -270,6 +272,7 @@ void fuseflow_destroy(fuseflow_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaFree(ctx->d_rig);
   cudaFree(ctx->d_rays);
+  cudaFree(ctx->d_mc);
   cudaFree(ctx->d_blocks);
   cudaFree(ctx->d_tables);
   cudaFree(ctx->d_out);
@@ -539,6 +542,40 @@ int fuseflow_fuse_frame_host(fuseflow_ctx* ctx, const void* const* depth, const 
     if (cudaStreamSynchronize(s) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
   }
   return st;
+}
+
+int fuseflow_mc_error(fuseflow_ctx* ctx, const float* pos, int64_t n_points,
+                      const void* const* depth, double occlusion_m, float* err_m,
+                      int32_t* n_visible, double* mc_m, int64_t* n_used, void* stream) {
+  if (!ctx || n_points < 0 || (n_points > 0 && !pos) || !depth || !mc_m || !n_used ||
+      !(occlusion_m >= 0.0))
+    return FUSEFLOW_ERR_INVALID_ARG;
+  for (int i = 0; i < ctx->n_cams; ++i)
+    if (!depth[i]) return FUSEFLOW_ERR_INVALID_ARG;
+  const int blocks = ffl::mc_blocks(n_points);
+  if (!ctx->d_mc && cudaMalloc(&ctx->d_mc, 1024 * (sizeof(double) + sizeof(long long))) != cudaSuccess) {
+    ctx->d_mc = nullptr;
+    return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  }
+  double* bsum = static_cast<double*>(ctx->d_mc);
+  long long* bcnt = reinterpret_cast<long long*>(bsum + 1024);
+  FramePtrs fp{};
+  for (int i = 0; i < ctx->n_cams; ++i) fp.depth[i] = depth[i];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<double> hs(blocks);
+  std::vector<long long> hc(blocks);
+  if (launch_mc(ctx->d_rig, fp, ctx->params.depth_format == FUSEFLOW_DEPTH_F32, pos, n_points,
+                ctx->params.depth_scale, occlusion_m, err_m, n_visible, bsum, bcnt, s) != cudaSuccess ||
+      cudaMemcpyAsync(hs.data(), bsum, sizeof(double) * blocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hc.data(), bcnt, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+  double sum = 0.0;
+  long long cnt = 0;
+  for (int b = 0; b < blocks; ++b) { sum += hs[b]; cnt += hc[b]; }
+  *n_used = cnt;
+  *mc_m = cnt ? sum / (double)cnt * ctx->params.depth_scale : std::nan("");
+  return FUSEFLOW_OK;
 }
 
 int fuseflow_set_trace(fuseflow_ctx* ctx, const fuseflow_trace* trace) {

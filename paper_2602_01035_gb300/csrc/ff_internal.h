@@ -100,6 +100,13 @@ inline int status_of_error(unsigned err) {
   return FUSEFLOW_OK;
 }
 
+// Eq. 12 over n points (world metres): per-point error (metres) and visible-camera count
+// (either may be NULL), per-block sums and counts in bsum/bcnt (mc_blocks(n) entries).
+int mc_blocks(long long n);
+cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, const float* pos,
+                      long long n, double unit_m, double occlusion_m, float* err, int* nvis,
+                      double* bsum, long long* bcnt, cudaStream_t s);
+
 int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
 int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);

@@ -2,23 +2,26 @@
 //
 // Launch sequence of one frame (all on the caller's stream):
 //   memset   frame counters + representative bitmap
-//   count    (a) decode + gate + back-project (Eq. 8, 9), coarse density n_c (Sec. II.5(1)c),
-//            per-block pixel counts and extent (Sec. II.5(1)b)
-//   assign   (b) consistency V (Eq. 4-7), omega = C V (Eq. 10) as mantissa/exponent;
-//            (c) level per coarse cell (Sec. II.5(1)d), cell key (Sec. II.5(1)e), fine
-//            hash insertion; (d) per (tile, cell): member count, representative
-//            (Sec. II.5(2)a), smallest weight exponent and exact fixed-point sums of
-//            omega, omega P, omega RGB (Eq. 11), written as one partial record
-//            and pushed onto its cell's list (cells own dense slots: coarse cell c owns
-//            8^level(c) consecutive slots, sized by the count step's last block)
+//   count    (a) decode + gate + back-project (Eq. 8, 9), coarse density n_c (Sec. II.5(1)c)
+//            from equal-cell runs merged across each warp, per-block pixel counts and
+//            extent (Sec. II.5(1)b)
+//   levels   level of each coarse cell (Sec. II.5(1)d) and its range of 8^level dense
+//            cell slots
+//   assign   per 32x16 tile: (b) consistency V (Eq. 4-7) in double-float, omega = C V
+//            (Eq. 10) as mantissa/exponent; (c) cell key (Sec. II.5(1)e) and dense slot;
+//            (d) per (tile, cell): member count, representative (Sec. II.5(2)a), smallest
+//            weight exponent and exact fixed-point sums of omega, omega P, omega RGB
+//            (Eq. 11), written as one partial record pushed onto its cell's list
 //   reduce   per cell: walk its partials, combine them, stage the fused cell, mark its
-//            representative; the used hash slots are cleared for the next frame
-//   scan     ranks of the representatives (output order) and frame statistics, one kernel
+//            representative; the used slots and coarse entries are cleared for the next frame
+//   scan     ranks of the representatives (output order) and frame statistics
 //   emit     fused cells in representative order
+// Outside the frame sequence: k_copyout (served frames: cloud into pinned host memory)
+// and k_mc (the multi-camera depth consistency error of Eq. 12 on a point set).
 //
-// Every reduction is order-independent (integer counts, max, min and fixed-point sums,
-// warp-level first, then shared memory, then one record per tile and cell), so the output
-// is bitwise reproducible.
+// Every reduction of the frame is order-independent (integer counts, max, min and
+// fixed-point sums), so its output is bitwise reproducible.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -1166,6 +1169,74 @@ __global__ void __launch_bounds__(kThreads) k_copyout(fuseflow_cloud src, HostOu
   }
 }
 
+// ------------------------------------------------------------------ Eq. 12 (MC error)
+// Per point P_k (world, metres): the cameras that see it (in front, nearest pixel inside
+// the image, valid D_i there) and the mean of |z(T_i P_k) - D_i(pi(T_i P_k))| over them.
+// Each block leaves the sum (depth units) and the number of points with a visible camera
+// in bsum/bcnt; the host adds the blocks in order, so the mean does not depend on timing.
+constexpr int kMcBlocks = 1024;
+
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_mc(const RigDev* __restrict__ rigp, FramePtrs fp,
+                                                 const float* __restrict__ pos, long long n,
+                                                 float inv_unit, float unit_m, float occl_u,
+                                                 float* err, int* nvis, double* bsum,
+                                                 long long* bcnt) {
+  __shared__ double s_sum[kThreads / 32];
+  __shared__ long long s_cnt[kThreads / 32];
+  const RigDev& rig = *rigp;
+  double tsum = 0.0;
+  long long tcnt = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const float P[3] = {__fmul_rn(pos[3 * k], inv_unit), __fmul_rn(pos[3 * k + 1], inv_unit),
+                        __fmul_rn(pos[3 * k + 2], inv_unit)};
+    float sum = 0.0f;
+    int vis = 0;
+    for (int i = 0; i < rig.n_cams; ++i) {
+      const CamDev& C = rig.cam[i];
+      const float d[3] = {__fsub_rn(P[0], C.cwc[0]), __fsub_rn(P[1], C.cwc[1]), __fsub_rn(P[2], C.cwc[2])};
+      float a[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)                     // T_i P = R (P - c), R = Rwc^T
+        a[q] = __fmaf_rn(C.Rwc[q], d[0], __fmaf_rn(C.Rwc[3 + q], d[1], __fmul_rn(C.Rwc[6 + q], d[2])));
+      if (!(a[2] > 0.0f)) continue;
+      const float fu = __fadd_rn(__fmaf_rn(C.fx, __fdiv_rn(a[0], a[2]), C.cx), 0.5f);
+      const float fv = __fadd_rn(__fmaf_rn(C.fy, __fdiv_rn(a[1], a[2]), C.cy), 0.5f);
+      if (!(fu >= 0.0f && fu < (float)C.W && fv >= 0.0f && fv < (float)C.H)) continue;
+      const int px = (int)fu, py = (int)fv;            // floor, both non-negative
+      const DT D = __ldg(static_cast<const DT*>(fp.depth[i]) + (long long)py * C.W + px);
+      if (!Depth<DT>::valid(D)) continue;
+      const float zD = Depth<DT>::z(D);
+      if (a[2] > __fadd_rn(zD, occl_u)) continue;       // hidden behind the observed surface
+      sum = __fadd_rn(sum, fabsf(__fsub_rn(a[2], zD)));
+      ++vis;
+    }
+    const float e = vis ? __fdiv_rn(sum, (float)vis) : __int_as_float(0x7fc00000);
+    if (err) err[k] = vis ? __fmul_rn(e, unit_m) : e;
+    if (nvis) nvis[k] = vis;
+    if (vis) {
+      tsum += (double)e;
+      ++tcnt;
+    }
+  }
+  // fixed-order block reduction
+  for (int o = 16; o > 0; o >>= 1) {
+    tsum += __shfl_down_sync(0xffffffffu, tsum, o);
+    tcnt += __shfl_down_sync(0xffffffffu, tcnt, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { s_sum[warp] = tsum; s_cnt[warp] = tcnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bs = 0.0;
+    long long bc = 0;
+    for (int w = 0; w < kThreads / 32; ++w) { bs += s_sum[w]; bc += s_cnt[w]; }
+    bsum[blockIdx.x] = bs;
+    bcnt[blockIdx.x] = bc;
+  }
+}
+
 __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   const unsigned n = max(fcap, ccap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1258,6 +1329,19 @@ cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cu
 
 cudaError_t launch_copyout(const fuseflow_cloud& src, const HostOutDev& dst, cudaStream_t s) {
   k_copyout<<<4 * 152, kThreads, 0, s>>>(src, dst);
+  return cudaGetLastError();
+}
+
+int mc_blocks(long long n) { return (int)std::max(1ll, std::min<long long>(kMcBlocks, (n + kThreads - 1) / kThreads)); }
+
+cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, const float* pos,
+                      long long n, double unit_m, double occlusion_m, float* err, int* nvis,
+                      double* bsum, long long* bcnt, cudaStream_t s) {
+  const int g = mc_blocks(n);
+  const float inv = (float)(1.0 / unit_m), um = (float)unit_m;
+  const float occl = (float)(occlusion_m / unit_m);      // +inf stays +inf
+  if (depth_f32) k_mc<float><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
+  else k_mc<uint16_t><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
   return cudaGetLastError();
 }
 

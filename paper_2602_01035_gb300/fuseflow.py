@@ -104,6 +104,9 @@ EXPORTS = {
                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fuseflow_mc_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p),
+                                    C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64), C.c_void_p]),
     "fuseflow_server_create": (C.c_int, [C.c_int64, C.POINTER(C.c_void_p)]),
     "fuseflow_server_add_rig": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_intrinsics),
                                           C.POINTER(fuseflow_extrinsics), C.c_int32,
@@ -280,6 +283,21 @@ def fuseflow_stage_name(stage: int) -> str:
 
 def fuseflow_status_string(status: int) -> str:
     return load().fuseflow_status_string(status).decode()
+
+
+MC_OCCLUSION_M = 0.05   # default occlusion margin of Eq. 12's visibility test, metres
+
+
+def fuseflow_mc_error(ctx, pos_ptr: int, n_points: int, depth_ptrs, err_ptr: int = 0,
+                      nvis_ptr: int = 0, stream: int = 0, occlusion_m: float = MC_OCCLUSION_M):
+    """(E_MC in metres, points used): Eq. 12 on n_points device positions."""
+    mc = C.c_double()
+    used = C.c_int64()
+    _check(load().fuseflow_mc_error(ctx, C.c_void_p(pos_ptr), n_points, _ptr_array(depth_ptrs),
+                                    float(occlusion_m), C.c_void_p(err_ptr), C.c_void_p(nvis_ptr),
+                                    C.byref(mc),
+                                    C.byref(used), C.c_void_p(stream)), "fuseflow_mc_error")
+    return mc.value, used.value
 
 
 def fuseflow_server_create(hbm_budget_bytes: int) -> C.c_void_p:

@@ -430,3 +430,71 @@ def test_golden_tiny_frame(oracle_mod):
     np.testing.assert_allclose(cells["pos"], gold["pos"], rtol=1e-12, atol=1e-15)
     for k in ("n_valid", "n_gated", "n_cells"):
         assert res["stats"][k] == gold["stats"][k]
+
+
+# ------------------------------------------------------------------ Eq. 12 (MC error)
+def _down_camera(x0, h, f=100.0, w=64, hgt=48):
+    """Camera at (x0, 0, h) looking straight down: x_cam = (x - x0, -y, h - z)."""
+    R = np.diag([1.0, -1.0, -1.0])
+    t = -R @ np.array([x0, 0.0, h])
+    return S.Camera(f, f, (w - 1) / 2, (hgt - 1) / 2, w, hgt, R, t)
+
+
+def test_mc_error_of_offsets_above_a_fronto_parallel_plane(oracle_mod):
+    """Depth 2 m everywhere under a camera 2 m above z = 0: a point at height d has
+    z(T P) = 2 - d, so its MC error is |d| exactly; points behind the camera, outside the
+    image or over an invalid depth sample are not visible and leave the mean."""
+    cam = _down_camera(0.0, 2.0)
+    rig = S.Rig([cam], "u16", 0.001)
+    depth = np.full((48, 64), 2000, np.uint16)
+    depth[0, 0] = 0                                   # invalid sample at pixel (0, 0)
+    corner = np.array([(0 - cam.cx) / cam.fx, -(0 - cam.cy) / cam.fy]) * 2.0
+    pts = np.array([[0.10, 0.05, 0.01], [-0.20, 0.10, 0.02], [0.0, 0.0, -0.03],
+                    [0.1, 0.1, 3.0],                  # behind the camera
+                    [50.0, 0.0, 0.0],                 # outside the image
+                    [corner[0], corner[1], 0.0]])     # lands on the invalid sample
+    r = oracle_mod.mc_error(rig, [depth], pts)
+    assert list(r["nvis"]) == [1, 1, 1, 0, 0, 0]
+    np.testing.assert_allclose(r["err_m"][:3], [0.01, 0.02, 0.03], rtol=0, atol=1e-12)
+    assert np.isnan(r["err_m"][3:]).all()
+    assert r["n_used"] == 3
+    assert abs(r["mc_m"] - 0.02) < 1e-12
+
+
+def test_mc_error_averages_over_the_visible_cameras(oracle_mod):
+    """Two downward cameras whose depth maps read 2.0 m and 2.1 m: a point at height d
+    (d > 0) has errors d and 0.1 + d, mean d + 0.05."""
+    rig = S.Rig([_down_camera(0.0, 2.0), _down_camera(0.3, 2.0)], "u16", 0.001)
+    depth = [np.full((48, 64), 2000, np.uint16), np.full((48, 64), 2100, np.uint16)]
+    pts = np.array([[0.15, 0.0, 0.01], [0.15, 0.05, 0.04]])
+    r = oracle_mod.mc_error(rig, depth, pts)
+    assert list(r["nvis"]) == [2, 2]
+    np.testing.assert_allclose(r["err_m"], [0.06, 0.09], rtol=0, atol=1e-12)
+    assert abs(r["mc_m"] - 0.075) < 1e-12
+
+
+def test_mc_error_of_a_noiseless_fused_plane_is_zero(oracle_mod):
+    """Two downward cameras over the plane z = 0 with exact depth: every fused point lies on
+    the plane, so Eq. 12 gives 0 for the fused cloud."""
+    rig = S.Rig([_down_camera(0.0, 2.0), _down_camera(0.2, 2.0)], "u16", 0.001)
+    depth = [np.full((48, 64), 2000, np.uint16) for _ in range(2)]
+    conf = [np.full((48, 64), 0.9, np.float32) for _ in range(2)]
+    rgb = [np.zeros((48, 64, 3), np.uint8) for _ in range(2)]
+    out = oracle_mod.fuse_frame(rig, S.Frame(depth, conf, rgb), {"n_min": 4}, points=False)
+    pos = out["cells"]["pos"]
+    assert len(pos) > 10
+    r = oracle_mod.mc_error(rig, depth, pos)
+    assert r["n_used"] == len(pos)
+    assert r["mc_m"] < 1e-12
+
+
+def test_mc_error_skips_points_hidden_behind_the_observed_surface(oracle_mod):
+    """A point 0.1 m under the plane lies 0.1 m behind the surface the camera sees: beyond a
+    0.05 m occlusion margin it is not visible; with no occlusion test its error is 0.1 m."""
+    rig = S.Rig([_down_camera(0.0, 2.0)], "u16", 0.001)
+    depth = [np.full((48, 64), 2000, np.uint16)]
+    pts = np.array([[0.1, 0.0, -0.1], [0.1, 0.0, -0.04]])
+    r = oracle_mod.mc_error(rig, depth, pts, occlusion_m=0.05)
+    assert list(r["nvis"]) == [0, 1] and abs(r["mc_m"] - 0.04) < 1e-12
+    r = oracle_mod.mc_error(rig, depth, pts, occlusion_m=np.inf)
+    assert list(r["nvis"]) == [1, 1] and abs(r["mc_m"] - 0.07) < 1e-12
