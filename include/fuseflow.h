@@ -163,6 +163,26 @@ int fuseflow_mc_error(fuseflow_ctx *ctx, const float *pos, int64_t n_points,
                       const void *const *depth, double occlusion_m, float *err_m,
                       int32_t *n_visible, double *mc_m, int64_t *n_used, void *stream);
 
+/* Weights of the confidence model of Eq. 3. */
+typedef struct {
+    double alpha, beta, gamma, delta;
+} fuseflow_conf_params;
+
+/* Eq. 3's printed constants: alpha = beta = 0.5, gamma = delta = 1. */
+void fuseflow_default_conf_params(fuseflow_conf_params *cp);
+
+/* Measurement confidence of Eq. 3 for callers without a confidence image: for every
+ * camera i, reads depth[i] (DEVICE, the context's depth format) and writes conf_out[i]
+ * (DEVICE float32 [H_i][W_i]).  Readings: depths in metres; G = |(g_x, g_y)| with g the
+ * central difference (z(x+1) - z(x-1)) / 2 where both neighbours are valid, the one-sided
+ * difference where one is, 0 where none is; sigma_local = the population variance (m^2)
+ * of the valid depths in the 3x3 window; C = (alpha / (1 + beta G) + gamma / (1 + delta
+ * sigma_local)) / (alpha + gamma), so that C stays in [0, 1] as Eq. 2 requires; C = 0 where
+ * the depth is invalid.  cp NULL selects the printed constants.  Asynchronous on `stream`.
+ * Returns INVALID_ARG, CUDA. */
+int fuseflow_confidence(fuseflow_ctx *ctx, const void *const *depth, float *const *conf_out,
+                        const fuseflow_conf_params *cp, void *stream);
+
 /* Registers (or, with NULL, clears) a per-pixel trace written by later fuse calls. */
 int fuseflow_set_trace(fuseflow_ctx *ctx, const fuseflow_trace *trace);
 

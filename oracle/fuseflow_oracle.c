@@ -564,3 +564,53 @@ int orc_mc_error(const orc_camera *cams, int32_t n, const orc_params *p,
     *n_used = used;
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------- Eq. 3 confidence */
+int orc_confidence(const void *depth, int32_t w, int32_t h, const orc_params *p, double alpha,
+                   double beta, double gamma, double delta, double *out) {
+    if (!depth || w < 1 || h < 1 || !p || !out || !(alpha + gamma > 0.0)) return ORC_ERR_ARG;
+    for (int32_t y = 0; y < h; ++y) {
+        for (int32_t x = 0; x < w; ++x) {
+            double z;
+            if (!depth_at(depth, p->depth_format, (int64_t)y * w + x, p->depth_scale, &z)) {
+                out[(int64_t)y * w + x] = 0.0;
+                continue;
+            }
+            /* depth gradient G from central (or one-sided) differences */
+            double g[2];
+            for (int axis = 0; axis < 2; ++axis) {
+                const int dx = axis == 0, dy = axis == 1;
+                double zm = 0.0, zp = 0.0;
+                const int xm = x - dx, ym = y - dy, xp = x + dx, yp = y + dy;
+                const int vm = xm >= 0 && ym >= 0 &&
+                               depth_at(depth, p->depth_format, (int64_t)ym * w + xm, p->depth_scale, &zm);
+                const int vp = xp < w && yp < h &&
+                               depth_at(depth, p->depth_format, (int64_t)yp * w + xp, p->depth_scale, &zp);
+                if (vm && vp) g[axis] = (zp - zm) / 2.0;
+                else if (vp) g[axis] = zp - z;
+                else if (vm) g[axis] = z - zm;
+                else g[axis] = 0.0;
+            }
+            const double G = sqrt(g[0] * g[0] + g[1] * g[1]);
+            /* local variance of the valid depths of the 3x3 window (two passes) */
+            double vals[9];
+            int n = 0;
+            for (int v = -1; v <= 1; ++v)
+                for (int u = -1; u <= 1; ++u) {
+                    const int xx = x + u, yy = y + v;
+                    double zz;
+                    if (xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                    if (depth_at(depth, p->depth_format, (int64_t)yy * w + xx, p->depth_scale, &zz))
+                        vals[n++] = zz;
+                }
+            double mean = 0.0, var = 0.0;
+            for (int k = 0; k < n; ++k) mean += vals[k];
+            mean /= n;
+            for (int k = 0; k < n; ++k) var += (vals[k] - mean) * (vals[k] - mean);
+            var /= n;
+            out[(int64_t)y * w + x] =
+                (alpha / (1.0 + beta * G) + gamma / (1.0 + delta * var)) / (alpha + gamma);
+        }
+    }
+    return ORC_OK;
+}

@@ -109,6 +109,16 @@ int orc_mc_error(const orc_camera *cams, int32_t n_cams, const orc_params *p,
                  double occlusion_m, double *err, int32_t *nvis, double *tie_px,
                  double *mc_m, int64_t *n_used);
 
+/* Eq. 3 confidence of one depth image (w x h, depth format and scale of p), written to
+ * out[h][w] (double).  Readings: depths in metres; G = |(g_x, g_y)|, g_x the central
+ * difference (z(x+1) - z(x-1)) / 2 when both neighbours are valid, the one-sided
+ * difference with the valid one otherwise, 0 with neither (same for g_y); sigma_local = the
+ * population variance (m^2) of the valid depths of the 3x3 window; C = (alpha / (1 + beta G)
+ * + gamma / (1 + delta sigma_local)) / (alpha + gamma), which keeps C in [0, 1] (Eq. 2);
+ * C = 0 where the depth itself is invalid. */
+int orc_confidence(const void *depth, int32_t w, int32_t h, const orc_params *p, double alpha,
+                   double beta, double gamma, double delta, double *out);
+
 #ifdef __cplusplus
 }
 #endif

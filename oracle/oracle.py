@@ -88,6 +88,9 @@ def _load():
                                      C.POINTER(C.c_void_p), C.c_void_p, C.c_int64, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                      C.POINTER(C.c_int64)]
+        lib.orc_confidence.restype = C.c_int
+        lib.orc_confidence.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(_Params),
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p]
         lib.orc_default_params.restype = None
         lib.orc_default_params.argtypes = [C.POINTER(_Params)]
         _lib = lib
@@ -212,6 +215,28 @@ def mc_error(rig, depth, points, occlusion_m: float = MC_OCCLUSION_M,
         raise RuntimeError(f"orc_mc_error failed with status {rc}")
     return {"err_m": err[:n], "nvis": nvis[:n], "tie_px": tie[:n], "mc_m": mc.value,
             "n_used": used.value}
+
+
+PAPER_CONF = {"alpha": 0.5, "beta": 0.5, "gamma": 1.0, "delta": 1.0}   # Eq. 3's constants
+
+
+def confidence(depth, depth_format: str, depth_scale: float, alpha=0.5, beta=0.5, gamma=1.0,
+               delta=1.0) -> np.ndarray:
+    """Eq. 3 confidence of one depth image (FP64 oracle)."""
+    lib = _load()
+    prm = _Params()
+    lib.orc_default_params(C.byref(prm))
+    prm.depth_format = DEPTH_FORMATS[depth_format]
+    prm.depth_scale = depth_scale
+    want = {"u16": np.uint16, "f32": np.float32, "f64": np.float64}[depth_format]
+    d = np.ascontiguousarray(depth, dtype=want)
+    h, w = d.shape
+    out = np.zeros((h, w), np.float64)
+    rc = lib.orc_confidence(d.ctypes.data, w, h, C.byref(prm), alpha, beta, gamma, delta,
+                            out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"orc_confidence failed with status {rc}")
+    return out
 
 
 def key_fields(key):

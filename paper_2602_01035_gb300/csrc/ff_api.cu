@@ -544,6 +544,45 @@ int fuseflow_fuse_frame_host(fuseflow_ctx* ctx, const void* const* depth, const 
   return st;
 }
 
+void fuseflow_default_conf_params(fuseflow_conf_params* cp) {
+  if (!cp) return;
+  cp->alpha = 0.5;
+  cp->beta = 0.5;
+  cp->gamma = 1.0;
+  cp->delta = 1.0;
+}
+
+int fuseflow_confidence(fuseflow_ctx* ctx, const void* const* depth, float* const* conf_out,
+                        const fuseflow_conf_params* cp, void* stream) {
+  if (!ctx || !depth || !conf_out) return FUSEFLOW_ERR_INVALID_ARG;
+  fuseflow_conf_params p;
+  fuseflow_default_conf_params(&p);
+  if (cp) p = *cp;
+  if (!(p.alpha >= 0.0) || !(p.beta >= 0.0) || !(p.gamma >= 0.0) || !(p.delta >= 0.0) ||
+      !(p.alpha + p.gamma > 0.0))
+    return FUSEFLOW_ERR_INVALID_ARG;
+  ConfArgs a{};
+  a.n_cams = ctx->n_cams;
+  a.scale = (float)ctx->params.depth_scale;
+  a.alpha = (float)p.alpha;
+  a.beta = (float)p.beta;
+  a.gamma = (float)p.gamma;
+  a.delta = (float)p.delta;
+  int max_w = 0, max_h = 0;
+  for (int i = 0; i < ctx->n_cams; ++i) {
+    if (!depth[i] || !conf_out[i]) return FUSEFLOW_ERR_INVALID_ARG;
+    a.depth[i] = depth[i];
+    a.out[i] = conf_out[i];
+    a.W[i] = ctx->intr[i].width;
+    a.H[i] = ctx->intr[i].height;
+    max_w = std::max(max_w, a.W[i]);
+    max_h = std::max(max_h, a.H[i]);
+  }
+  return launch_confidence(a, ctx->params.depth_format == FUSEFLOW_DEPTH_F32, max_w, max_h,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FUSEFLOW_OK : FUSEFLOW_ERR_CUDA;
+}
+
 int fuseflow_mc_error(fuseflow_ctx* ctx, const float* pos, int64_t n_points,
                       const void* const* depth, double occlusion_m, float* err_m,
                       int32_t* n_visible, double* mc_m, int64_t* n_used, void* stream) {

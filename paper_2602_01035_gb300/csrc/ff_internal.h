@@ -107,6 +107,18 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
                       long long n, double unit_m, double occlusion_m, float* err, int* nvis,
                       double* bsum, long long* bcnt, cudaStream_t s);
 
+// Eq. 3 confidence producer: per camera, depth in, float32 confidence out.
+struct ConfArgs {
+  const void* depth[kMaxCams];
+  float* out[kMaxCams];
+  int W[kMaxCams], H[kMaxCams];
+  int n_cams;
+  float scale;                   // metres per depth unit
+  float alpha, beta, gamma, delta;
+};
+cudaError_t launch_confidence(const ConfArgs& a, bool depth_f32, int max_w, int max_h,
+                              cudaStream_t s);
+
 int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
 int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);

@@ -1237,6 +1237,99 @@ __global__ void __launch_bounds__(kThreads) k_mc(const RigDev* __restrict__ rigp
   }
 }
 
+// ------------------------------------------------------------------ Eq. 3 confidence
+// One 128x8 pixel tile per block; the tile and its one-pixel halo are staged in shared
+// memory (raw depth samples), each thread computes four pixels of one row, 32 apart, so
+// that the float32 stores of a warp are contiguous.  Depth gradient G: central difference
+// where both neighbours are valid, one-sided with one, 0 with none; sigma_local: the
+// population variance of the window's valid depths, exact in integer depth units for
+// uint16 depth (two passes in float32 for float32 depth); C is normalised by alpha + gamma
+// and is 0 where the depth is invalid.
+constexpr int kConfW = 128, kConfH = 8;
+
+template <typename DT>
+__device__ __forceinline__ float conf_pixel(const DT (*t)[kConfW + 2], int r, int c, float scale,
+                                            float alpha, float beta, float gamma, float delta) {
+  const DT d0 = t[r][c];
+  if (!Depth<DT>::valid(d0)) return 0.0f;
+  float g[2];
+#pragma unroll
+  for (int axis = 0; axis < 2; ++axis) {
+    const DT dm = axis == 0 ? t[r][c - 1] : t[r - 1][c];
+    const DT dp = axis == 0 ? t[r][c + 1] : t[r + 1][c];
+    const bool vm = Depth<DT>::valid(dm), vp = Depth<DT>::valid(dp);
+    const float zm = Depth<DT>::z(dm), zp = Depth<DT>::z(dp), z0 = Depth<DT>::z(d0);
+    const float diff = vm && vp ? __fmul_rn(__fsub_rn(zp, zm), 0.5f)
+                     : vp ? __fsub_rn(zp, z0) : vm ? __fsub_rn(z0, zm) : 0.0f;
+    g[axis] = __fmul_rn(diff, scale);
+  }
+  const float G = sqrtf(__fmaf_rn(g[0], g[0], __fmul_rn(g[1], g[1])));
+  float var;
+  if constexpr (sizeof(DT) == 2) {
+    long long s1 = 0, s2 = 0;
+    int n = 0;
+#pragma unroll
+    for (int v = -1; v <= 1; ++v)
+#pragma unroll
+      for (int u = -1; u <= 1; ++u) {
+        const long long d = (long long)t[r + v][c + u];
+        if (d) { s1 += d; s2 += d * d; ++n; }
+      }
+    // n^2 var = n s2 - s1^2, exact in integers
+    var = __fmul_rn(__fdiv_rn((float)(n * s2 - s1 * s1), (float)(n * n)), __fmul_rn(scale, scale));
+  } else {
+    float s1 = 0.0f;
+    int n = 0;
+#pragma unroll
+    for (int v = -1; v <= 1; ++v)
+#pragma unroll
+      for (int u = -1; u <= 1; ++u) {
+        const DT d = t[r + v][c + u];
+        if (Depth<DT>::valid(d)) { s1 = __fadd_rn(s1, d); ++n; }
+      }
+    const float mean = __fdiv_rn(s1, (float)n);
+    float s2 = 0.0f;
+#pragma unroll
+    for (int v = -1; v <= 1; ++v)
+#pragma unroll
+      for (int u = -1; u <= 1; ++u) {
+        const DT d = t[r + v][c + u];
+        if (Depth<DT>::valid(d)) { const float e = __fsub_rn(d, mean); s2 = __fmaf_rn(e, e, s2); }
+      }
+    var = __fmul_rn(__fdiv_rn(s2, (float)n), __fmul_rn(scale, scale));
+  }
+  const float a = __fdiv_rn(alpha, __fmaf_rn(beta, G, 1.0f));
+  const float b = __fdiv_rn(gamma, __fmaf_rn(delta, var, 1.0f));
+  return __fdiv_rn(__fadd_rn(a, b), __fadd_rn(alpha, gamma));
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_confidence(ConfArgs a) {
+  __shared__ DT t[kConfH + 2][kConfW + 2];
+  const int cam = blockIdx.z;
+  const int W = a.W[cam], H = a.H[cam];
+  const int x0 = blockIdx.x * kConfW, y0 = blockIdx.y * kConfH;
+  if (x0 >= W || y0 >= H) return;                       // uniform over the block
+  const DT* __restrict__ dep = static_cast<const DT*>(a.depth[cam]);
+  // invalid outside the image (0 for uint16, 0.0f for float32 depth)
+  for (int i = threadIdx.x; i < (kConfH + 2) * (kConfW + 2); i += kThreads) {
+    const int r = i / (kConfW + 2), c = i - r * (kConfW + 2);
+    const int x = x0 - 1 + c, y = y0 - 1 + r;
+    t[r][c] = (x >= 0 && y >= 0 && x < W && y < H) ? __ldcs(dep + (long long)y * W + x) : (DT)0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 32, tx = threadIdx.x & 31;
+  const int y = y0 + ty;
+  if (y >= H) return;
+  float* __restrict__ out = a.out[cam] + (long long)y * W;
+#pragma unroll
+  for (int k = 0; k < kConfW / 32; ++k) {
+    const int c = tx + 32 * k, x = x0 + c;
+    if (x < W)
+      __stcs(out + x, conf_pixel<DT>(t, ty + 1, c + 1, a.scale, a.alpha, a.beta, a.gamma, a.delta));
+  }
+}
+
 __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   const unsigned n = max(fcap, ccap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1329,6 +1422,14 @@ cudaError_t launch_init_tables(const Tables& t, unsigned fcap, unsigned ccap, cu
 
 cudaError_t launch_copyout(const fuseflow_cloud& src, const HostOutDev& dst, cudaStream_t s) {
   k_copyout<<<4 * 152, kThreads, 0, s>>>(src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_confidence(const ConfArgs& a, bool depth_f32, int max_w, int max_h,
+                              cudaStream_t s) {
+  const dim3 g((max_w + kConfW - 1) / kConfW, (max_h + kConfH - 1) / kConfH, a.n_cams);
+  if (depth_f32) k_confidence<float><<<g, kThreads, 0, s>>>(a);
+  else k_confidence<uint16_t><<<g, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,11 @@ class fuseflow_trace(C.Structure):
                 ("nview", C.c_void_p), ("key", C.c_void_p)]
 
 
+class fuseflow_conf_params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("delta", C.c_double)]
+
+
 class fuseflow_host_cloud(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("rgb", C.c_void_p), ("weight", C.c_void_p),
                 ("count", C.c_void_p), ("rep", C.c_void_p), ("key", C.c_void_p),
@@ -104,6 +109,9 @@ EXPORTS = {
                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fuseflow_default_conf_params": (None, [C.POINTER(fuseflow_conf_params)]),
+    "fuseflow_confidence": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(fuseflow_conf_params), C.c_void_p]),
     "fuseflow_mc_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p),
                                     C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.c_void_p]),
@@ -283,6 +291,16 @@ def fuseflow_stage_name(stage: int) -> str:
 
 def fuseflow_status_string(status: int) -> str:
     return load().fuseflow_status_string(status).decode()
+
+
+def fuseflow_confidence(ctx, depth_ptrs, out_ptrs, stream: int = 0, **weights) -> None:
+    """Eq. 3 confidence of every camera's depth image into float32 device buffers."""
+    cp = fuseflow_conf_params()
+    load().fuseflow_default_conf_params(C.byref(cp))
+    for k, v in weights.items():
+        setattr(cp, k, v)
+    _check(load().fuseflow_confidence(ctx, _ptr_array(depth_ptrs), _ptr_array(out_ptrs),
+                                      C.byref(cp), C.c_void_p(stream)), "fuseflow_confidence")
 
 
 MC_OCCLUSION_M = 0.05   # default occlusion margin of Eq. 12's visibility test, metres

@@ -498,3 +498,48 @@ def test_mc_error_skips_points_hidden_behind_the_observed_surface(oracle_mod):
     assert list(r["nvis"]) == [0, 1] and abs(r["mc_m"] - 0.04) < 1e-12
     r = oracle_mod.mc_error(rig, depth, pts, occlusion_m=np.inf)
     assert list(r["nvis"]) == [1, 1] and abs(r["mc_m"] - 0.07) < 1e-12
+
+
+# ------------------------------------------------------------------ Eq. 3 (confidence)
+def test_confidence_of_a_constant_depth_is_one(oracle_mod):
+    d = np.full((7, 9), 2500, np.uint16)
+    c = oracle_mod.confidence(d, "u16", 0.001)
+    np.testing.assert_allclose(c, 1.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_confidence_of_a_linear_ramp_has_closed_form(oracle_mod, axis):
+    """z = 2 + b t along one image axis: the central difference is exactly b, every interior
+    3x3 window holds b (-1, 0, 1) three times (population variance 2 b^2 / 3), border pixels
+    use one-sided differences (still b) and their 2x3 windows (variance b^2 / 4)."""
+    b = 0.004                                          # 4 mm per pixel
+    h, w = 6, 8
+    t = np.arange(w if axis == 0 else h)
+    ramp = 2000 + 4 * t                                # millimetres
+    d = np.tile(ramp, (h, 1)) if axis == 0 else np.tile(ramp[:, None], (1, w))
+    c = oracle_mod.confidence(d.astype(np.uint16), "u16", 0.001)
+    a_, be, ga, de = 0.5, 0.5, 1.0, 1.0
+    f = lambda var: (a_ / (1 + be * b) + ga / (1 + de * var)) / (a_ + ga)
+    interior = c[1:-1, 1:-1]
+    np.testing.assert_allclose(interior, f(2 * b * b / 3), rtol=1e-13)
+    edge = c[1:-1, 0] if axis == 0 else c[0, 1:-1]     # first column / row along the ramp
+    np.testing.assert_allclose(edge, f(b * b / 4), rtol=1e-13)
+
+
+def test_confidence_of_invalid_and_isolated_pixels(oracle_mod):
+    """Invalid depth gives C = 0; a valid pixel with no valid neighbour has G = 0 and a
+    one-sample window (variance 0), so C = 1; the paper's constants keep C in [0, 1]."""
+    d = np.zeros((5, 5), np.float32)
+    d[2, 2] = 1.7
+    c = oracle_mod.confidence(d, "f32", 1.0)
+    assert c[2, 2] == 1.0 and c.sum() == 1.0
+    rng = np.random.default_rng(3)
+    noisy = rng.uniform(0.5, 8.0, size=(40, 50)).astype(np.float32)
+    noisy[rng.random((40, 50)) < 0.1] = 0.0
+    c = oracle_mod.confidence(noisy, "f32", 1.0)
+    assert c.min() >= 0.0 and c.max() <= 1.0 and (c[noisy == 0] == 0).all()
+    # a depth step lowers the confidence on both sides of the edge
+    step = np.full((6, 10), 2000, np.uint16)
+    step[:, 5:] = 3000
+    c = oracle_mod.confidence(step, "u16", 0.001)
+    assert c[3, 4] < 0.9 and c[3, 5] < 0.9 and c[3, 0] == 1.0 and c[3, 9] == 1.0
