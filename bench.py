@@ -356,6 +356,29 @@ def run_ours(args, rank, world, local_rank):
                  "achieved_gbs": round(path_bytes / (ms / 1e3 / (args.steps * FPS)) / 1e9, 1),
                  "frac": round(path_bytes / (ms / 1e3 / (args.steps * FPS)) / 1e9 / peak, 4)}
 
+    # ------------------------------------------------------------ Eq. 3 confidence producer
+    # (an optional input stage: callers without a confidence image), timed alone over the
+    # pool's depth maps (inputs larger than L2), CUDA events on the launching stream
+    conf_out = [torch.empty(x.shape, dtype=torch.float32, device=dev) for x in pool[0].depth]
+    conf_ptrs = [t.data_ptr() for t in conf_out]
+    for i in range(3):
+        F.fuseflow_confidence(ff.ctx, dtensors[i % len(dtensors)][3], conf_ptrs, sh)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_conf = 200
+    c0.record(stream)
+    for i in range(n_conf):
+        F.fuseflow_confidence(ff.ctx, dtensors[i % len(dtensors)][3], conf_ptrs, sh)
+    c1.record(stream)
+    torch.cuda.synchronize(dev)
+    conf_ms = c0.elapsed_time(c1) / n_conf
+    conf_bytes = (depth_bytes + 4) * px
+    stages["confidence"] = {"bound": "hbm", "achieved": round(conf_bytes / (conf_ms / 1e3) / 1e9, 1),
+                            "peak": peak, "unit": "GB/s",
+                            "frac": round(conf_bytes / (conf_ms / 1e3) / 1e9 / peak, 4),
+                            "traffic": traffic.get("confidence"), "launch_ms": round(conf_ms, 5),
+                            "algorithmic_bytes_per_launch": int(conf_bytes), "peak_source": peak_kind,
+                            "note": "optional producer of Eq. 3, not part of the fused step"}
+
     # ------------------------------------------------------------ end to end (host buffers)
     # The public serving API on this rig: frames from pinned host memory, results into
     # pinned host arrays, `slots` frames in flight (copies overlap other frames' kernels).

@@ -568,6 +568,7 @@ int fuseflow_confidence(fuseflow_ctx* ctx, const void* const* depth, float* cons
   a.beta = (float)p.beta;
   a.gamma = (float)p.gamma;
   a.delta = (float)p.delta;
+  a.inv_ag = (float)(1.0 / (p.alpha + p.gamma));
   int max_w = 0, max_h = 0;
   for (int i = 0; i < ctx->n_cams; ++i) {
     if (!depth[i] || !conf_out[i]) return FUSEFLOW_ERR_INVALID_ARG;

@@ -115,6 +115,7 @@ struct ConfArgs {
   int n_cams;
   float scale;                   // metres per depth unit
   float alpha, beta, gamma, delta;
+  float inv_ag;                  // 1 / (alpha + gamma)
 };
 cudaError_t launch_confidence(const ConfArgs& a, bool depth_f32, int max_w, int max_h,
                               cudaStream_t s);

@@ -1238,95 +1238,111 @@ __global__ void __launch_bounds__(kThreads) k_mc(const RigDev* __restrict__ rigp
 }
 
 // ------------------------------------------------------------------ Eq. 3 confidence
-// One 128x8 pixel tile per block; the tile and its one-pixel halo are staged in shared
-// memory (raw depth samples), each thread computes four pixels of one row, 32 apart, so
-// that the float32 stores of a warp are contiguous.  Depth gradient G: central difference
-// where both neighbours are valid, one-sided with one, 0 with none; sigma_local: the
-// population variance of the window's valid depths, exact in integer depth units for
-// uint16 depth (two passes in float32 for float32 depth); C is normalised by alpha + gamma
-// and is 0 where the depth is invalid.
-constexpr int kConfW = 128, kConfH = 8;
-
-template <typename DT>
-__device__ __forceinline__ float conf_pixel(const DT (*t)[kConfW + 2], int r, int c, float scale,
-                                            float alpha, float beta, float gamma, float delta) {
-  const DT d0 = t[r][c];
-  if (!Depth<DT>::valid(d0)) return 0.0f;
-  float g[2];
-#pragma unroll
-  for (int axis = 0; axis < 2; ++axis) {
-    const DT dm = axis == 0 ? t[r][c - 1] : t[r - 1][c];
-    const DT dp = axis == 0 ? t[r][c + 1] : t[r + 1][c];
-    const bool vm = Depth<DT>::valid(dm), vp = Depth<DT>::valid(dp);
-    const float zm = Depth<DT>::z(dm), zp = Depth<DT>::z(dp), z0 = Depth<DT>::z(d0);
-    const float diff = vm && vp ? __fmul_rn(__fsub_rn(zp, zm), 0.5f)
-                     : vp ? __fsub_rn(zp, z0) : vm ? __fsub_rn(z0, zm) : 0.0f;
-    g[axis] = __fmul_rn(diff, scale);
-  }
-  const float G = sqrtf(__fmaf_rn(g[0], g[0], __fmul_rn(g[1], g[1])));
-  float var;
-  if constexpr (sizeof(DT) == 2) {
-    long long s1 = 0, s2 = 0;
-    int n = 0;
-#pragma unroll
-    for (int v = -1; v <= 1; ++v)
-#pragma unroll
-      for (int u = -1; u <= 1; ++u) {
-        const long long d = (long long)t[r + v][c + u];
-        if (d) { s1 += d; s2 += d * d; ++n; }
-      }
-    // n^2 var = n s2 - s1^2, exact in integers
-    var = __fmul_rn(__fdiv_rn((float)(n * s2 - s1 * s1), (float)(n * n)), __fmul_rn(scale, scale));
-  } else {
-    float s1 = 0.0f;
-    int n = 0;
-#pragma unroll
-    for (int v = -1; v <= 1; ++v)
-#pragma unroll
-      for (int u = -1; u <= 1; ++u) {
-        const DT d = t[r + v][c + u];
-        if (Depth<DT>::valid(d)) { s1 = __fadd_rn(s1, d); ++n; }
-      }
-    const float mean = __fdiv_rn(s1, (float)n);
-    float s2 = 0.0f;
-#pragma unroll
-    for (int v = -1; v <= 1; ++v)
-#pragma unroll
-      for (int u = -1; u <= 1; ++u) {
-        const DT d = t[r + v][c + u];
-        if (Depth<DT>::valid(d)) { const float e = __fsub_rn(d, mean); s2 = __fmaf_rn(e, e, s2); }
-      }
-    var = __fmul_rn(__fdiv_rn(s2, (float)n), __fmul_rn(scale, scale));
-  }
-  const float a = __fdiv_rn(alpha, __fmaf_rn(beta, G, 1.0f));
-  const float b = __fdiv_rn(gamma, __fmaf_rn(delta, var, 1.0f));
-  return __fdiv_rn(__fadd_rn(a, b), __fadd_rn(alpha, gamma));
-}
+// One 128x32 pixel tile per block, staged with its one-pixel halo in shared memory (raw
+// depth samples; vector loads for the interior columns).  Each thread computes four
+// consecutive pixels in each of four rows, 8 apart, and stores each quadruple as one float4;
+// the four windows share one load of their 3x6 samples, and each window's variance is taken
+// relative to its centre depth.  Depth
+// gradient G: central difference where both neighbours are valid, one-sided with one, 0
+// with none; sigma_local: population variance of the window's valid depths (m^2); C is
+// normalised by alpha + gamma and is 0 where the depth is invalid.
+constexpr int kConfW = 128, kConfH = 32;
 
 template <typename DT>
 __global__ void __launch_bounds__(kThreads) k_confidence(ConfArgs a) {
-  __shared__ DT t[kConfH + 2][kConfW + 2];
+  constexpr int kVec = 16 / sizeof(DT);                  // samples per 16-byte load
+  constexpr int kRowVecs = kConfW / kVec;
+  constexpr int kOff = kVec;                             // tile column c at c + kOff: the
+  constexpr int kRow = kConfW + 2 * kVec;                // interior starts 16-byte aligned
+  __shared__ __align__(16) DT t[kConfH + 2][kRow];
   const int cam = blockIdx.z;
   const int W = a.W[cam], H = a.H[cam];
   const int x0 = blockIdx.x * kConfW, y0 = blockIdx.y * kConfH;
   if (x0 >= W || y0 >= H) return;                       // uniform over the block
   const DT* __restrict__ dep = static_cast<const DT*>(a.depth[cam]);
-  // invalid outside the image (0 for uint16, 0.0f for float32 depth)
-  for (int i = threadIdx.x; i < (kConfH + 2) * (kConfW + 2); i += kThreads) {
-    const int r = i / (kConfW + 2), c = i - r * (kConfW + 2);
-    const int x = x0 - 1 + c, y = y0 - 1 + r;
-    t[r][c] = (x >= 0 && y >= 0 && x < W && y < H) ? __ldcs(dep + (long long)y * W + x) : (DT)0;
+  const bool vec_ok = (W % kVec) == 0 && ((reinterpret_cast<uintptr_t>(dep) & 15) == 0);
+  // interior columns: rows y0-1 .. y0+8, 16-byte loads where the whole vector is inside
+  for (int i = threadIdx.x; i < (kConfH + 2) * kRowVecs; i += kThreads) {
+    const int r = i / kRowVecs, v = i - r * kRowVecs;
+    const int y = y0 - 1 + r, x = x0 + v * kVec;
+    DT* dst = &t[r][kOff + v * kVec];
+    if (y >= 0 && y < H && vec_ok && x + kVec <= W) {
+      *reinterpret_cast<uint4*>(dst) = __ldcs(reinterpret_cast<const uint4*>(dep + (long long)y * W + x));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kVec; ++k)
+        dst[k] = (y >= 0 && y < H && x + k < W) ? dep[(long long)y * W + x + k] : (DT)0;
+    }
+  }
+  // halo columns x0-1 and x0+128 (invalid outside the image)
+  if (threadIdx.x < 2 * (kConfH + 2)) {
+    const int r = threadIdx.x >> 1, side = threadIdx.x & 1;
+    const int y = y0 - 1 + r, x = side ? x0 + kConfW : x0 - 1;
+    t[r][side ? kOff + kConfW : kOff - 1] = (y >= 0 && y < H && x >= 0 && x < W) ? dep[(long long)y * W + x] : (DT)0;
   }
   __syncthreads();
-  const int ty = threadIdx.x / 32, tx = threadIdx.x & 31;
-  const int y = y0 + ty;
-  if (y >= H) return;
-  float* __restrict__ out = a.out[cam] + (long long)y * W;
+  const int tx = threadIdx.x & 31, xb = x0 + 4 * tx;
+  if (xb >= W) return;
+  const int c0 = kOff + 4 * tx - 1;                       // smem column of pixel xb - 1
+  for (int ty = threadIdx.x / 32; ty < kConfH; ty += kThreads / 32) {
+    const int y = y0 + ty;
+    if (y >= H) break;
+    // the 3x6 samples of the thread's four windows, once, as depth (z) and validity
+    float zz[3][6];
+    bool vv[3][6];
 #pragma unroll
-  for (int k = 0; k < kConfW / 32; ++k) {
-    const int c = tx + 32 * k, x = x0 + c;
-    if (x < W)
-      __stcs(out + x, conf_pixel<DT>(t, ty + 1, c + 1, a.scale, a.alpha, a.beta, a.gamma, a.delta));
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const DT d = t[ty + r][c0 + c];
+        vv[r][c] = Depth<DT>::valid(d);
+        zz[r][c] = vv[r][c] ? Depth<DT>::z(d) : 0.0f;
+      }
+    float res[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (!vv[1][p + 1]) { res[p] = 0.0f; continue; }
+      const float z0 = zz[1][p + 1];
+      float g[2];
+#pragma unroll
+      for (int axis = 0; axis < 2; ++axis) {
+        const bool vm = axis == 0 ? vv[1][p] : vv[0][p + 1];
+        const bool vp = axis == 0 ? vv[1][p + 2] : vv[2][p + 1];
+        const float zm = axis == 0 ? zz[1][p] : zz[0][p + 1];
+        const float zp = axis == 0 ? zz[1][p + 2] : zz[2][p + 1];
+        const float diff = vm && vp ? __fmul_rn(__fsub_rn(zp, zm), 0.5f)
+                         : vp ? __fsub_rn(zp, z0) : vm ? __fsub_rn(z0, zm) : 0.0f;
+        g[axis] = __fmul_rn(diff, a.scale);
+      }
+      const float G2 = __fmaf_rn(g[0], g[0], __fmul_rn(g[1], g[1]));
+      const float G = G2 > 0.0f ? __fmul_rn(G2, rsqrtf(G2)) : 0.0f;   // |g|, a few ulp
+      // window variance relative to the centre sample (one pass: the centre is one of the
+      // samples, so the cancellation costs at most a factor 9 in relative precision)
+      float n = 0.0f, sm = 0.0f, sq = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float e = vv[r][p + c] ? __fsub_rn(zz[r][p + c], z0) : 0.0f;
+          n = __fadd_rn(n, vv[r][p + c] ? 1.0f : 0.0f);
+          sm = __fadd_rn(sm, e);
+          sq = __fmaf_rn(e, e, sq);
+        }
+      const float rn = __fdividef(1.0f, n);
+      const float var = __fmul_rn(fmaxf(__fmul_rn(__fsub_rn(sq, __fmul_rn(__fmul_rn(sm, sm), rn)), rn), 0.0f),
+                                  __fmul_rn(a.scale, a.scale));
+      const float ta = __fdividef(a.alpha, __fmaf_rn(a.beta, G, 1.0f));
+      const float tb = __fdividef(a.gamma, __fmaf_rn(a.delta, var, 1.0f));
+      res[p] = __fmul_rn(__fadd_rn(ta, tb), a.inv_ag);
+    }
+    float* __restrict__ out = a.out[cam] + (long long)y * W + xb;
+    if (xb + 4 <= W && (W & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.out[cam]) & 15) == 0)) {
+      __stcs(reinterpret_cast<float4*>(out), make_float4(res[0], res[1], res[2], res[3]));
+    } else {
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        if (xb + p < W) out[p] = res[p];
+    }
   }
 }
 
