@@ -51,6 +51,7 @@ void orc_default_params(orc_params *p) {
     p->band_m = 1e-5;
     p->band_px = 1e-6;
     p->band_az = 1e-6;
+    p->top_k = 0;
 }
 
 /* ---------------------------------------------------------------- small linear algebra */
@@ -204,7 +205,7 @@ int orc_fuse_frame(const orc_camera *cams, int32_t n, const orc_params *p,
                    int64_t cell_capacity, orc_stats *st) {
     if (!cams || n < 1 || !p || !depth || !conf || !rgb || !st) return ORC_ERR_ARG;
     if (p->k_views < 1 || p->sigma_m <= 0 || p->coarse_cell_m <= 0 || p->max_level < 0 ||
-        p->max_level > 14 || p->n_min < 1 || p->depth_scale <= 0)
+        p->max_level > 14 || p->n_min < 1 || p->depth_scale <= 0 || p->top_k < 0)
         return ORC_ERR_ARG;
     const int K = p->k_views < n ? p->k_views : n;
     const int K1 = K - 1;
@@ -469,23 +470,50 @@ int orc_fuse_frame(const orc_camera *cams, int32_t n, const orc_params *p,
             }
             start[n_cells] = n_pts;
             qsort(order, (size_t)n_cells, sizeof(rep_item), cmp_rep);
-            for (int64_t o = 0; o < n_cells; ++o) {
+            uint32_t *fused = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_pts > 0 ? n_pts : 1));
+            for (int64_t o = 0; fused && o < n_cells; ++o) {
                 const int64_t c0 = order[o].cell;
                 const int64_t a = start[c0], b = start[c0 + 1];
+                /* the members that enter Eq. 11: all of them, or (Sec. II.5(2)a) the top_k
+                   by C, ties to the lowest pixel index, taken by repeated selection */
+                int64_t nf = 0;
+                if (p->top_k == 0 || b - a <= p->top_k) {
+                    for (int64_t t = a; t < b; ++t) fused[nf++] = items[t].g;
+                } else {
+                    for (int k = 0; k < p->top_k; ++k) {
+                        int64_t best = -1;
+                        float bc = 0.0f;
+                        for (int64_t t = a; t < b; ++t) {
+                            const uint32_t g = items[t].g;
+                            int taken = 0;
+                            for (int64_t q = 0; q < nf; ++q) taken |= fused[q] == g;
+                            if (taken) continue;
+                            const float Cg = conf_of(conf, off, n, g);
+                            if (best < 0 || Cg > bc || (Cg == bc && g < (uint32_t)best)) {
+                                best = g;
+                                bc = Cg;
+                            }
+                        }
+                        fused[nf++] = (uint32_t)best;
+                    }
+                }
                 double lmax = -INFINITY, W = 0.0;
                 uint32_t fl = 0;
                 for (int64_t t = a; t < b; ++t) {
                     uint32_t g = items[t].g;
-                    if (lw[g] > lmax) lmax = lw[g];
-                    W += om[g];
                     if (flag[g] & 8) fl |= ORC_CELL_BOUNDARY;
                     if (flag[g] & 16) fl |= ORC_CELL_AMBIGUOUS_LEVEL;
+                }
+                for (int64_t q = 0; q < nf; ++q) {
+                    const uint32_t g = fused[q];
+                    if (lw[g] > lmax) lmax = lw[g];
+                    W += om[g];
                     if (flag[g] & 4) fl |= ORC_CELL_TIE;
                 }
                 /* Eq. 11, normalised; weights scaled by the largest one */
                 double sw = 0.0, sp[3] = {0, 0, 0}, sc[3] = {0, 0, 0};
-                for (int64_t t = a; t < b; ++t) {
-                    const uint32_t g = items[t].g;
+                for (int64_t q = 0; q < nf; ++q) {
+                    const uint32_t g = fused[q];
                     const int ci = camera_of(off, n, g);
                     const uint8_t *px = rgb[ci] + 3 * (g - off[ci]);
                     double w = exp(lw[g] - lmax);
@@ -505,6 +533,8 @@ int orc_fuse_frame(const orc_camera *cams, int32_t n, const orc_params *p,
                 }
                 if (cells->flags) cells->flags[o] = fl;
             }
+            if (!fused) rc = ORC_ERR_NOMEM;
+            free(fused);
             free(order);
             free(start);
         }

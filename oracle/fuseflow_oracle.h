@@ -45,6 +45,8 @@ typedef struct {
     double band_m;         /* report points within band_m of a cell boundary */
     double band_px;        /* report projections within band_px of a half-pixel tie */
     double band_az;        /* report projections with |a_z| below band_az metres */
+    int32_t top_k;         /* Sec. II.5(2)a: fuse only the top_k members of a cell by C
+                              (ties to the lowest pixel index); 0 = every member */
 } orc_params;
 
 /* Per-pixel outputs, arrays of n_pixels entries in global pixel order

@@ -35,7 +35,7 @@ class _Params(C.Structure):
                 ("coarse_cell_m", C.c_double), ("max_level", C.c_int32), ("n_min", C.c_int32),
                 ("depth_format", C.c_int32), ("use_conf", C.c_int32), ("depth_scale", C.c_double),
                 ("use_consistency", C.c_int32), ("row_step", C.c_int32), ("band_m", C.c_double),
-                ("band_px", C.c_double), ("band_az", C.c_double)]
+                ("band_px", C.c_double), ("band_az", C.c_double), ("top_k", C.c_int32)]
 
 
 _P = C.c_void_p

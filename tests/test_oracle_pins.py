@@ -543,3 +543,52 @@ def test_confidence_of_invalid_and_isolated_pixels(oracle_mod):
     step[:, 5:] = 3000
     c = oracle_mod.confidence(step, "u16", 0.001)
     assert c[3, 4] < 0.9 and c[3, 5] < 0.9 and c[3, 0] == 1.0 and c[3, 9] == 1.0
+
+
+# ------------------------------------------------------------------ Sec. II.5(2)a top-k variant
+def _topk_case():
+    rig = S.tiny_rig(n=3, width=40, height=30, spread_deg=20.0)
+    fr = S.random_frame(rig, seed=41, zero_frac=0.02)
+    return rig, fr
+
+
+def test_top_k_fuses_the_k_most_confident_members(oracle_mod):
+    """Brute force over the oracle's per-point outputs: each cell's W, position and colour
+    come from its top-3 members by C (ties to the lowest pixel index); count, key and
+    representative are those of the full cell."""
+    rig, fr = _topk_case()
+    full = oracle_mod.fuse_frame(rig, fr, {"n_min": 2})
+    top = oracle_mod.fuse_frame(rig, fr, {"n_min": 2, "top_k": 3})
+    assert np.array_equal(full["cells"]["key"], top["cells"]["key"])
+    assert np.array_equal(full["cells"]["count"], top["cells"]["count"])
+    assert np.array_equal(full["cells"]["rep"], top["cells"]["rep"])
+    conf = np.concatenate([c.ravel() for c in fr.conf])
+    rgb = np.concatenate([c.reshape(-1, 3) for c in fr.rgb]).astype(np.float64)
+    key, pw, om = top["key"], top["pw"], top["omega"]
+    n_multi = 0
+    for c, k in enumerate(top["cells"]["key"]):
+        g = np.nonzero(key == k)[0]
+        order = sorted(g, key=lambda q: (-conf[q], q))[:3]
+        n_multi += len(g) > 3
+        w = om[order]
+        assert abs(top["cells"]["weight"][c] - w.sum()) <= 1e-12 * max(1.0, w.sum())
+        if w.sum() > 0:
+            np.testing.assert_allclose(top["cells"]["pos"][c], (w[:, None] * pw[order]).sum(0) / w.sum(),
+                                       rtol=0, atol=1e-12)
+            np.testing.assert_allclose(top["cells"]["rgb"][c], (w[:, None] * rgb[order]).sum(0) / w.sum(),
+                                       rtol=0, atol=1e-9)
+    assert n_multi > 20                                   # cells where the selection matters
+
+
+def test_top_k_limits(oracle_mod):
+    """top_k = 1 fuses the representative alone; top_k at least the largest cell is the
+    full method."""
+    rig, fr = _topk_case()
+    full = oracle_mod.fuse_frame(rig, fr, {"n_min": 2})
+    one = oracle_mod.fuse_frame(rig, fr, {"n_min": 2, "top_k": 1})
+    big = oracle_mod.fuse_frame(rig, fr, {"n_min": 2, "top_k": int(full["cells"]["count"].max())})
+    for k in ("pos", "weight", "rgb"):
+        np.testing.assert_array_equal(big["cells"][k], full["cells"][k])
+    rep = one["cells"]["rep"]
+    np.testing.assert_array_equal(one["cells"]["pos"], one["pw"][rep])
+    np.testing.assert_allclose(one["cells"]["weight"], one["omega"][rep], rtol=1e-15)
