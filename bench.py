@@ -300,6 +300,44 @@ def run_ours(args, rank, world, local_rank):
         for c in ctxs[1:]:
             c.close()
 
+    # ------------------------------------------------------------ Sec. II.5(2)a top-3 variant
+    # (consistency and weights for each cell's 3 most confident members only): same frames,
+    # plain path, CUDA events around the step
+    top3 = None
+    if True:
+        ff3 = F.FuseFlow(rig, top_k=3)
+
+        def top3_step():
+            for i in range(FPS):
+                t = dtensors[i % len(dtensors)]
+                F.fuseflow_fuse_frame(ff3.ctx, t[3], t[4], t[5], sh)
+
+        for _ in range(max(args.warmup, 1)):
+            top3_step()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        a0.record(stream)
+        for _ in range(args.steps):
+            top3_step()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        tms = max_over_ranks(a0.elapsed_time(a1), world, dev)
+        s3, st3 = ff3.stats(sh, check=False)
+        F.fuseflow_enable_stage_timing(ff3.ctx, True)
+        for i in range(min(FPS, 64)):
+            t = dtensors[i % len(dtensors)]
+            F.fuseflow_fuse_frame(ff3.ctx, t[3], t[4], t[5], sh)
+        st_ms, n_t = F.fuseflow_read_stage_times(ff3.ctx)
+        top3 = {"value": round(job_rate(args.steps * FPS * px, world, tms), 1), "unit": "px/s",
+                "frames_per_s": round(job_rate(args.steps * FPS, world, tms), 2),
+                "ms_per_step": round(tms / args.steps, 4), "vs_plain": round(ms / tms, 4),
+                "status_ok": s3 == F.FUSEFLOW_OK, "cells_per_frame": int(st3.n_cells),
+                "stage_ms": {k: round(v / max(n_t, 1), 5) for k, v in st_ms.items()},
+                "path": "top_k = 3: each cell fuses its 3 most confident members, whose "
+                        "consistency is computed per cell in the reduce step"}
+        ff3.close()
+
     # ------------------------------------------------------------ per-frame latency (plain path)
     lat = []
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -462,7 +500,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "path_roofline": path_roof,
         "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "stage_roofline": stages,
-        "batched": batched, "serving": serving, "other_configs": configs,
+        "batched": batched, "top3_variant": top3, "serving": serving, "other_configs": configs,
         "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
         "cells_per_frame": int(n_cells), "status_ok": ok_status,
         "clocks": clocks, "cpu_baseline": cpu,

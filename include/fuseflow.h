@@ -69,7 +69,9 @@ typedef struct {
     int32_t use_conf;       /* 0 = ablation "no measurement confidence": no gate, omega = V */
     double depth_scale;     /* metres per depth unit; 0.001 for millimetre uint16 */
     int32_t use_consistency;/* 0 = ablation "no distance consistency": V = 1 */
-    int32_t reserved0;
+    int32_t top_k;          /* Sec. II.5(2)a: fuse only the top_k members of each cell by C
+                               (ties to the lowest pixel index), with consistency computed
+                               for those alone; 0 = every member (default); at most 7 */
     int64_t max_cells;      /* output capacity in cells; 0 = max(65536, pixels / 8) */
 } fuseflow_params;
 
@@ -100,7 +102,9 @@ typedef struct {
 
 /* Optional per-pixel trace of the last fused frame (caller-owned device arrays of
  * n_pixels entries; any pointer may be NULL).  Pixels that are not gated get
- * nview = -1, key = ~0 and NaN in the float arrays. */
+ * nview = -1, key = ~0 and NaN in the float arrays.  With top_k > 0 the weights of a
+ * frame are computed for the cells' top-k members only, after the trace is written: gated
+ * pixels get nview = -2 and omega, e are left untouched. */
 typedef struct {
     float *pw;              /* [n][3] world point of Eq. 8, metres */
     float *omega;           /* Eq. 10 joint weight (may underflow to 0 in float32) */

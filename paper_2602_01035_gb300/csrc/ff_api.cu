@@ -142,6 +142,7 @@ int validate(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr, i
     return FUSEFLOW_ERR_INVALID_ARG;
   if (!(p->depth_scale > 0) || !finite(p->depth_scale)) return FUSEFLOW_ERR_INVALID_ARG;
   if (p->max_cells < 0 || p->max_cells > (1ll << 30)) return FUSEFLOW_ERR_INVALID_ARG;
+  if (p->top_k < 0 || p->top_k > kMaxTopK) return FUSEFLOW_ERR_INVALID_ARG;
   return FUSEFLOW_OK;
 }
 
@@ -165,6 +166,7 @@ void build_rig(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr,
   const double sig_u = params->sigma_m / unit;
   if (k1 > 0) split(1.0 / (sig_u * sig_u * k1), rig.einv_h, rig.einv_l);
   rig.depth_f32 = params->depth_format == FUSEFLOW_DEPTH_F32;
+  rig.top_k = params->top_k;
   int nr = 0, np = 0;
   long long off = 0;
   for (int i = 0; i < n_cams; ++i) {
@@ -322,6 +324,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
 
   // ---------------------------------------------------------------- launch geometry
   ctx->geo.n_cams = n_cams;
+  ctx->geo.top_k = params->top_k;
   ctx->geo.depth_f32 = rig->depth_f32;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -417,6 +420,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     od.max_cells = ctx->max_cells;
     od.s0_m = params->coarse_cell_m;
     od.unit_m = unit;
+  od.unit_f = (float)unit;
     if (cudaMemcpy(ctx->d_rig, rig, sizeof(RigDev), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_rays, rays.data(), sizeof(float2) * rays.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_blocks, bconst.data(), sizeof(BlockConst) * (size_t)n_cams,
@@ -876,6 +880,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
     return FUSEFLOW_ERR_CUDA;
 
   geo.n_cams = n_cams;
+  geo.top_k = params->top_k;
   geo.depth_f32 = rig.depth_f32;
   geo.count_blocks_x = (int)((max_px + 2047) / 2048);
   geo.count_chunks = 1;
@@ -899,6 +904,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   od.max_cells = max_cells;
   od.s0_m = params->coarse_cell_m;
   od.unit_m = unit;
+  od.unit_f = (float)unit;
   FramePtrs fp{};
   for (int i = 0; i < n_cams; ++i) {
     fp.depth[i] = depth[i];

@@ -18,6 +18,7 @@ namespace ffl {
 
 constexpr int kMaxCams = 64;
 constexpr int kMaxK1 = 8;
+constexpr int kMaxTopK = 7;              // top-k keys travel in a partial record's 7 sums
 constexpr unsigned long long kKeyEmpty = ~0ull;
 constexpr uint32_t kSlotNone = 0xffffffffu;
 constexpr int kFixShift = 36;            // per-cell fixed point: largest member weight ~ 2^36
@@ -64,7 +65,7 @@ struct RigDev {
   float inv_s0u;                 // 1 / s0 in 1 / depth units
   float einv_h, einv_l;          // 1 / (sigma_u^2 (K-1)) as ff
   int depth_f32;
-  int pad;
+  int top_k;                     // Sec. II.5(2)a variant: fuse the top_k members only (0: all)
   long long n_px;
   CamDev cam[kMaxCams];
   PairDev pair[kMaxCams * kMaxK1];

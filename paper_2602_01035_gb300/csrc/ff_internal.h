@@ -59,6 +59,7 @@ struct OutDev {
   unsigned long long* key;
   long long max_cells;
   float s0_m;                    // coarse edge, metres
+  float unit_f;                  // metres per depth unit, float32
   double unit_m;                 // metres per depth unit
 };
 
@@ -66,8 +67,9 @@ struct Geometry {
   int n_cams;
   int depth_f32;
   int count_blocks_x;            // blocks per camera of the coarse-count step (max over cams)
-  int count_chunks;              // 1024-pixel chunks per block of the coarse-count step
+  int count_chunks;              // 2048-pixel chunks per block of the coarse-count step
   int emit_blocks;
+  int top_k;                     // Sec. II.5(2)a variant (0: every member is fused)
   TileIndex tiles;               // assign-step tiles
 };
 

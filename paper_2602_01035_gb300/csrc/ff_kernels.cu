@@ -151,17 +151,44 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 }
 
 // Sum over the K-1 neighbour views of d_ij^2 (Eq. 6) in depth units^2, as ff (sh, sl).
-// Pixel (lx, ly) of the block's tile at z-depth z; the transform into view j (Eq. 4) uses
-// the tile's separable pair rays staged in shared memory (s_pr), so that
+// A pixel at z-depth z; the transform into view j (Eq. 4) uses the pixel's separable pair
+// rays (from the tile's shared-memory copy or the global tables), so that
 // a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff product and one ff sum per component.  Views go in groups of kViewGroup: every view of
 // a group is projected and its depth gather issued before any residual is formed, so the
 // gathers of a group overlap instead of following one another.
 constexpr int kViewGroup = 3;
 
-template <typename DT>
-__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const float4* s_pr,
+// Pair rays of a tile staged in shared memory (pixel (lx, ly) of the tile).
+struct TilePairRays {
+  const float4* s_pr;
+  int lx, ly;
+  __device__ __forceinline__ void operator()(int q, const PairDev&, float4& a01, float4& a2,
+                                             float4& b01, float4& b2) const {
+    const float4* pr = s_pr + q * kPrayPerView;
+    a01 = pr[lx];
+    a2 = pr[kTileW + lx];
+    b01 = pr[2 * kTileW + ly];
+    b2 = pr[2 * kTileW + kTileH + ly];
+  }
+};
+
+// Pair rays read from the global tables (pixel (x, y) of the camera).
+struct GlobalPairRays {
+  const float4* pray;
+  int x, y;
+  __device__ __forceinline__ void operator()(int, const PairDev& P, float4& a01, float4& a2,
+                                             float4& b01, float4& b2) const {
+    a01 = __ldg(pray + P.ga + 2 * x);
+    a2 = __ldg(pray + P.ga + 2 * x + 1);
+    b01 = __ldg(pray + P.gb + 2 * y);
+    b2 = __ldg(pray + P.gb + 2 * y + 1);
+  }
+};
+
+template <typename DT, typename PR>
+__device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const PR& prays,
                                              const float2* __restrict__ rays,
-                                             const FramePtrs& fp, float z, int lx, int ly,
+                                             const FramePtrs& fp, float z,
                                              float& sh, float& sl, int& nview) {
   sh = 0.0f;
   sl = 0.0f;
@@ -182,9 +209,8 @@ __device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const
       if (q >= k1) continue;
       const PairDev& P = bc.pair[q];
       const CamDev& J = bc.nb[q];
-      const float4* pr = s_pr + q * kPrayPerView;
-      const float4 a01 = pr[lx], a2 = pr[kTileW + lx];
-      const float4 b01 = pr[2 * kTileW + ly], b2 = pr[2 * kTileW + kTileH + ly];
+      float4 a01, a2, b01, b2;
+      prays(q, P, a01, a2, b01, b2);
       ff_ray_affine(a01.x, a01.y, b01.x, b01.y, z, P.th[0], P.tl[0], ah[g][0], al[g][0]);
       ff_ray_affine(a01.z, a01.w, b01.z, b01.w, z, P.th[1], P.tl[1], ah[g][1], al[g][1]);
       ff_ray_affine(a2.x, a2.y, b2.x, b2.y, z, P.th[2], P.tl[2], ah[g][2], al[g][2]);
@@ -236,6 +262,33 @@ __device__ __forceinline__ void residual_sum(const BlockConst& bc, int k1, const
       ++nview;
     }
   }
+}
+
+// Eq. 7 and 10 from the residual sum (sh, sl): omega = C' exp(-e) = mu 2^-m with
+// e = m ln 2 + f, f in [0, ln 2), so that mu never underflows (C' = C, or 1 without the
+// confidence term).  Returns e (high part) for traces.
+__device__ __forceinline__ float joint_weight(const RigDev& rig, int k1, float sh, float sl,
+                                              float c, float& mu, int& m) {
+  float eh = 0.0f, el = 0.0f;
+  if (rig.use_cons && k1 > 0) {
+    fast_two_sum(sh, sl, sh, sl);
+    two_prod(sh, rig.einv_h, eh, el);                                  // Eq. 7 exponent
+    el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
+    fast_two_sum(eh, el, eh, el);
+  }
+  m = 0;
+  float fh = eh, fl = el;
+  if (eh > 0.0f) {
+    m = (int)floorf(__fmul_rn(fminf(eh, 1.0e9f), kInvLn2));
+    const float mf = (float)m;
+    float p, pe;
+    two_prod(mf, kLn2H, p, pe);
+    fh = __fsub_rn(eh, p);
+    fl = __fsub_rn(__fsub_rn(el, pe), __fmul_rn(mf, kLn2L));
+  }
+  const float base = rig.use_conf ? c : 1.0f;                          // Eq. 10
+  mu = __fmul_rn(__fmul_rn(base, expf(-fh)), __fsub_rn(1.0f, fl));
+  return eh;
 }
 
 // ------------------------------------------------------------------ count step
@@ -485,6 +538,7 @@ constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pix
 // Distinct cells of a tile with shared-memory accumulators; the members of any further
 // cell (sparse, noisy tiles only) file one single-member partial each.
 constexpr int kAssignNL = kTilePx / 2;
+static_assert(kMaxTopK * 8 <= 14 * 4, "a cell's top-k keys fit in its 14 split-sum words");
 constexpr int kAssignBlocksPerSM = 4;      // registers (64) and shared memory allow four
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 static_assert(sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev)) <= 2 * 4 * kThreads,
@@ -556,7 +610,10 @@ __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, in
   y0 = (local / tiles_x) * kTileH;
 }
 
-template <typename DT>
+// TOPK: the Sec. II.5(2)a variant; members are keyed and counted as usual, but a tile keeps
+// each cell's top-k members by C (packed (ordered(C) << 32) | ~g keys) instead of weights;
+// the consistency and weights of those members are computed per cell by k_reduce_topk.
+template <typename DT, bool TOPK>
 __global__ void __launch_bounds__(kThreads, kAssignBlocksPerSM)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m, TileIndex ti) {
@@ -630,7 +687,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       const int idx = threadIdx.x + r * kThreads;
       pri[r] = -1;
       prv[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (idx >= k1 * kPrayPerView) continue;
+      if (TOPK || idx >= k1 * kPrayPerView) continue;
       const int q = idx / kPrayPerView, o = idx - q * kPrayPerView;
       const int base = ti.pray[cam] + 2 * q * (Wp + Hp);
       int src = -1;
@@ -763,29 +820,15 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     unsigned ch = 0u;
     ulonglong2 ce = make_ulonglong2(kKeyEmpty, 0ull);
     if (has[j]) ce = coarse_probe(t, ck, ch);
-    float sh = 0.0f, sl = 0.0f, eh = 0.0f, el = 0.0f;
-    int nview = 0;
-    if (rig.use_cons && k1 > 0) {
-      residual_sum<DT>(bc, k1, reinterpret_cast<const float4*>(smem + kSmPR), rays, fp, z,
-                       x - td.x0, y - td.y0, sh, sl, nview);
-      fast_two_sum(sh, sl, sh, sl);
-      two_prod(sh, rig.einv_h, eh, el);                               // Eq. 7 exponent
-      el = __fmaf_rn(sh, rig.einv_l, __fmaf_rn(sl, rig.einv_h, el));
-      fast_two_sum(eh, el, eh, el);
+    float sh = 0.0f, sl = 0.0f, eh = 0.0f;
+    int nview = 0, m = 0;
+    if constexpr (!TOPK) {
+      if (rig.use_cons && k1 > 0)
+        residual_sum<DT>(bc, k1, TilePairRays{reinterpret_cast<const float4*>(smem + kSmPR),
+                                              x - td.x0, y - td.y0},
+                         rays, fp, z, sh, sl, nview);
+      eh = joint_weight(rig, k1, sh, sl, c, mu[j], m);
     }
-    // omega = C exp(-e) = mu 2^-m, e = m ln2 + f, f in [0, ln2): mu never underflows
-    int m = 0;
-    float fh = eh, fl = el;
-    if (eh > 0.0f) {
-      m = (int)floorf(__fmul_rn(fminf(eh, 1.0e9f), kInvLn2));
-      const float mf = (float)m;
-      float p, pe;
-      two_prod(mf, kLn2H, p, pe);
-      fh = __fsub_rn(eh, p);
-      fl = __fsub_rn(__fsub_rn(el, pe), __fmul_rn(mf, kLn2L));
-    }
-    const float base = rig.use_conf ? c : 1.0f;                       // Eq. 10
-    mu[j] = __fmul_rn(__fmul_rn(base, expf(-fh)), __fsub_rn(1.0f, fl));
     mexp[j] = m;
     cord[j] = ordered(c);
     if (trace) {
@@ -794,9 +837,13 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
         tr.pw[3 * gi[j] + 1] = P[1] * unit_m;
         tr.pw[3 * gi[j] + 2] = P[2] * unit_m;
       }
-      if (tr.e) tr.e[gi[j]] = eh;
-      if (tr.omega) tr.omega[gi[j]] = ldexpf(mu[j], -m);
-      if (tr.nview) tr.nview[gi[j]] = nview;
+      if (!TOPK) {
+        if (tr.e) tr.e[gi[j]] = eh;
+        if (tr.omega) tr.omega[gi[j]] = ldexpf(mu[j], -m);
+        if (tr.nview) tr.nview[gi[j]] = nview;
+      } else if (tr.nview) {                    // the top-k variant weighs cells' top-k only:
+        tr.nview[gi[j]] = -2;                   // gated, weight not evaluated here
+      }
     }
     if (has[j]) {
       // Sec. II.5(1)e: cell key, its dense slot, and the point's offset inside the cell
@@ -831,14 +878,22 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
               s_ek[e] = fk;
               s_ep[e] = (unsigned)h;
               s_gmin[e] = 0xffffffffu;
+              if constexpr (TOPK) {             // the entry's top-k list (u64 view of s_acc)
+                unsigned long long* top = reinterpret_cast<unsigned long long*>(s_acc) + e * kMaxTopK;
 #pragma unroll
-              for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
+                for (int q = 0; q < kMaxTopK; ++q) top[q] = 0ull;
+              } else {
+#pragma unroll
+                for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
+              }
             }
           }
           // Sec. II.5(2)a: members, largest C, smallest weight exponent
           atomicAdd(&s_cntp[h], 1u);
-          atomicMax(&s_cmaxp[h], cord[j]);
-          atomicMin(&s_minp[h], mexp[j]);
+          if (!TOPK) {
+            atomicMax(&s_cmaxp[h], cord[j]);
+            atomicMin(&s_minp[h], mexp[j]);
+          }
         }
       }
     }
@@ -856,6 +911,36 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     if (!has[j]) continue;
     const int h = hpos[j], e = s_fi[h];
     const bool alone = e >= kAssignNL;
+    if constexpr (TOPK) {
+      // Sec. II.5(2)a: insert the member into its cell's sorted top-k list; each slot keeps
+      // the largest key that reaches it and passes the smaller one down, so the list ends
+      // as the k largest keys whatever the order of the atomics
+      unsigned long long key = ((unsigned long long)cord[j] << 32) | (unsigned)(~(unsigned)gi[j]);
+      if (!alone) {
+        unsigned long long* top = reinterpret_cast<unsigned long long*>(s_acc) + e * kMaxTopK;
+        for (int q = 0; q < rig.top_k && key; ++q) {
+          const unsigned long long old = atomicMax(&top[q], key);
+          key = old < key ? old : key;
+        }
+      } else {                                  // a single-member partial of its own
+        Partial p;
+        p.slot = s_fk[h];
+        p.count = 1u;
+        p.mmin = 0;
+        p.rep = key;
+        p.s[0] = key;
+#pragma unroll
+        for (int a = 1; a < 7; ++a) p.s[a] = 0ull;
+        const unsigned pi = atomicAdd(&t.cnt->n_partials, 1u);
+        if (pi >= t.max_partials) {
+          atomicOr(&t.cnt->error, kErrPartials);
+        } else if (file_partial(t, p, fkey[j], pi)) {
+          const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
+          if (n < t.max_slots) t.fused[n] = p.slot;
+        }
+      }
+      continue;
+    }
     if (!alone && cord[j] == s_cmaxp[h]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
     const int sh = alone ? 0 : mexp[j] - s_minp[h];
     const float w = sh > 62 ? 0.0f : __fmul_rn(mu[j], pow2f(kFixShift - sh));
@@ -912,12 +997,20 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
         Partial p;
         p.slot = slot = s_fk[h];
         p.count = s_cntp[h];
-        p.mmin = s_minp[h];
-        p.rep = ((unsigned long long)s_cmaxp[h] << 32) | (unsigned)(~s_gmin[e]);
+        if constexpr (TOPK) {
+          const unsigned long long* top = reinterpret_cast<const unsigned long long*>(s_acc) + e * kMaxTopK;
+          p.mmin = 0;
+          p.rep = top[0];
 #pragma unroll
-        for (int a = 0; a < 7; ++a)
-          p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
-                   s_acc[(2 * a) * kAssignNL + e];
+          for (int a = 0; a < 7; ++a) p.s[a] = top[a];
+        } else {
+          p.mmin = s_minp[h];
+          p.rep = ((unsigned long long)s_cmaxp[h] << 32) | (unsigned)(~s_gmin[e]);
+#pragma unroll
+          for (int a = 0; a < 7; ++a)
+            p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
+                     s_acc[(2 * a) * kAssignNL + e];
+        }
         first = file_partial(t, p, s_ek[e], pi);
       }
     }
@@ -988,6 +1081,128 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
         if (head != kSlotNone) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));
       }
       // ready for the next frame: head = none, mmin = INT_MAX (one 8-byte store)
+      reinterpret_cast<unsigned long long*>(&t.frec[slot])[1] =
+          ((unsigned long long)(unsigned)INT_MAX << 32) | kSlotNone;
+    }
+    if (i < n_coarse) {
+      const unsigned cs = t.cused[i];
+      t.coarse[cs].key = kKeyEmpty;
+      t.coarse[cs].count = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ top-k reduce
+// Sec. II.5(2) variant, per cell: merge the tiles' top-k lists (the k largest packed
+// (ordered(C) << 32) | ~g keys of the union: order-independent), then for each of the
+// cell's k representatives recompute the world point (Eq. 8, the same float32 sequence as
+// the other steps), its consistency over its camera's K-1 views (Eq. 4-7, double-float,
+// global pair rays) and omega = C V (Eq. 10), and fuse them (Eq. 11, normalised, weights
+// scaled by the largest).  Members are counted over the whole cell; the representative is
+// the cell's top member.
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_reduce_topk(const RigDev* __restrict__ rigp,
+                                                          const float2* __restrict__ rays,
+                                                          FramePtrs fp, Tables t, OutDev out) {
+  const RigDev& rig = *rigp;
+  const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
+  const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
+  const unsigned n_part = min(t.cnt->n_partials, t.max_partials);
+  const unsigned n = max(n_cells, n_coarse);
+  const int K = rig.top_k;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < n_cells) {
+      const unsigned slot = t.fused[i];
+      const SlotRec rec = t.frec[slot];
+      unsigned long long top[kMaxTopK];
+#pragma unroll
+      for (int q = 0; q < kMaxTopK; ++q) top[q] = 0ull;
+      unsigned count = 0u, steps = 0u;
+      for (unsigned p = rec.head; p != kSlotNone && steps <= n_part; ++steps) {
+        const Partial P = t.part[p];
+        count += P.count;
+        for (int a = 0; a < K; ++a) {           // insert P.s[a] into the sorted list
+          unsigned long long key = P.s[a];
+#pragma unroll
+          for (int q = 0; q < kMaxTopK; ++q) {
+            if (q < K && key > top[q]) {
+              const unsigned long long tmp = top[q];
+              top[q] = key;
+              key = tmp;
+            }
+          }
+        }
+        p = P.next;
+      }
+      if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
+      // weights and world points of the representatives
+      float mu[kMaxTopK], P3[kMaxTopK][3], col[kMaxTopK][3];
+      int mx[kMaxTopK];
+      int mmin = INT_MAX, nr = 0;
+#pragma unroll
+      for (int q = 0; q < kMaxTopK; ++q) {      // sorted: the filled entries come first
+        mu[q] = 0.0f;
+        mx[q] = 0;
+        if (q >= K || !top[q]) continue;
+        const unsigned g = ~(unsigned)(top[q] & 0xffffffffull);
+        if ((long long)g >= rig.n_px) {         // not a pixel: a corrupted list (reported)
+          atomicOr(&t.cnt->error, kErrList);
+          top[q] = 0ull;
+          continue;
+        }
+        int cam = 0;
+        for (int c = 1; c < rig.n_cams; ++c)
+          if ((long long)g >= rig.cam[c].off) cam = c;
+        const CamDev& C = rig.cam[cam];
+        const long long li = (long long)g - C.off;
+        const int y = (int)(li / C.W), x = (int)(li - (long long)y * C.W);
+        const float z = Depth<DT>::z(static_cast<const DT*>(fp.depth[cam])[li]);
+        const float c = fp.conf[cam][li];
+        const uint8_t* px = fp.rgb[cam] + 3 * li;
+        world_point(C, z, __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P3[q]);
+        float sh = 0.0f, sl = 0.0f;
+        int nview = 0;
+        if (rig.use_cons && rig.k1 > 0)
+          residual_sum<DT>(t.bconst[cam], rig.k1, GlobalPairRays{t.pray, x, y}, rays, fp, z, sh,
+                           sl, nview);
+        joint_weight(rig, rig.k1, sh, sl, c, mu[q], mx[q]);
+        mmin = min(mmin, mx[q]);
+        col[q][0] = px[0];
+        col[q][1] = px[1];
+        col[q][2] = px[2];
+        ++nr;
+      }
+      CellOut cell;
+      float sw = 0.0f, sp[3] = {0.0f, 0.0f, 0.0f}, sc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < kMaxTopK; ++q) {      // Eq. 11, weights relative to the largest
+        if (q >= nr) continue;
+        const int sh = mx[q] - mmin;
+        const float w = sh > 126 ? 0.0f : __fmul_rn(mu[q], pow2f(-sh));
+        sw = __fadd_rn(sw, w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          sp[a] = __fmaf_rn(w, P3[q][a], sp[a]);
+          sc[a] = __fmaf_rn(w, col[q][a], sc[a]);
+        }
+      }
+      const float inv = nr ? __frcp_rn(sw) : __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        cell.pos[a] = __fmul_rn(__fmul_rn(sp[a], inv), out.unit_f);
+        cell.rgb[a] = __fmul_rn(sc[a], inv);
+      }
+      cell.weight = nr ? ldexpf(sw, -min(mmin, 1 << 30)) : 0.0f;
+      cell.count = count;
+      const bool have = nr > 0 && top[0] != 0ull;
+      const unsigned g = have ? ~(unsigned)(top[0] & 0xffffffffull) : 0xffffffffu;
+      cell.rep = g;
+      cell.pad = 0u;
+      cell.key = rec.key;
+      if ((long long)i < out.max_cells) {
+        t.staged[i] = cell;
+        if (have) atomicOr(&t.bitmap[g >> 5], 1u << (g & 31));   // g < n_px (checked above)
+      }
       reinterpret_cast<unsigned long long*>(&t.frec[slot])[1] =
           ((unsigned long long)(unsigned)INT_MAX << 32) | kSlotNone;
     }
@@ -1367,8 +1582,11 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                          cudaEvent_t* ev) {
   static bool attr_set = false;
   if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_assign<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)assign_smem(kMaxK1));
+    cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)assign_smem(kMaxK1));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_assign<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)assign_smem(kMaxK1));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1381,10 +1599,17 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                                                                        geo.count_chunks);
   k_levels<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(2);
-  k_assign<DT><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(rig, rays, fp, t, tr, (float)out.unit_m,
-                                                        geo.tiles);
-  mark(3);
-  k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  if (geo.top_k) {
+    k_assign<DT, true><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
+                                                                   (float)out.unit_m, geo.tiles);
+    mark(3);
+    k_reduce_topk<DT><<<geo.emit_blocks, kThreads, 0, s>>>(rig, rays, fp, t, out);
+  } else {
+    k_assign<DT, false><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(rig, rays, fp, t, tr,
+                                                                               (float)out.unit_m, geo.tiles);
+    mark(3);
+    k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  }
   mark(4);
   k_scan<<<t.n_wblocks, 1024, 0, s>>>(t, out);
   mark(5);

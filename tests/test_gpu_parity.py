@@ -111,6 +111,30 @@ def test_sparse_tiles_overflow_the_shared_accumulators(ffmod, oracle_mod):
     assert rep["n_cells_matched"] > 10000
 
 
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_top_k_variant(ffmod, oracle_mod, k):
+    """Sec. II.5(2)a: each cell fuses only its k most confident members; consistency and
+    weights are computed for those alone."""
+    rig, _, fr = S.config2(frame=4)
+    rep, gpu, orc = _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"top_k": k})
+    assert rep["n_cells_matched"] > 5000
+
+
+@pytest.mark.parametrize("n,w,h,fmt,seed", [(3, 70, 45, "u16", 51), (2, 33, 17, "f32", 52),
+                                            (4, 100, 61, "u16", 53)])
+def test_top_k_variant_ragged(ffmod, oracle_mod, n, w, h, fmt, seed):
+    scale = 1.0 if fmt == "f32" else 0.001
+    rig = S.tiny_rig(n=n, width=w, height=h, depth_format=fmt, depth_scale=scale, spread_deg=25.0)
+    fr = S.random_frame(rig, seed=seed, zero_frac=0.05, flying_frac=0.01)
+    _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"top_k": 3, "n_min": 4})
+
+
+def test_top_k_variant_benchmark_rig(ffmod, oracle_mod):
+    rig, _, fr = S.config3(frame=0)
+    rep, _, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"top_k": 3})
+    assert rep["n_cells_matched"] > 100000
+
+
 def test_empty_and_all_gated_out(ffmod, oracle_mod):
     rig = S.tiny_rig(n=2, width=40, height=30)
     z = [np.zeros((30, 40), np.uint16) for _ in range(2)]
