@@ -153,10 +153,11 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 // Sum over the K-1 neighbour views of d_ij^2 (Eq. 6) in depth units^2, as ff (sh, sl).
 // A pixel at z-depth z; the transform into view j (Eq. 4) uses the pixel's separable pair
 // rays (from the tile's shared-memory copy or the global tables), so that
-// a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff product and one ff sum per component.  Views go in groups of kViewGroup: every view of
-// a group is projected and its depth gather issued before any residual is formed, so the
-// gathers of a group overlap instead of following one another.
-constexpr int kViewGroup = 3;
+// a = z (A(x) + B(y)) + t_ji costs one ff sum, one ff product and one ff sum per component.
+// Views go in groups of kViewGroup: every view of a group is projected and its depth gather
+// issued before any residual is formed.  Groups of one measure fastest on GB300 (larger
+// groups spill at four blocks per SM and grow the code past the instruction cache).
+constexpr int kViewGroup = 1;
 
 // Pair rays of a tile staged in shared memory (pixel (lx, ly) of the tile).
 struct TilePairRays {
