@@ -614,7 +614,7 @@ __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, in
 // TOPK: the Sec. II.5(2)a variant; members are keyed and counted as usual, but a tile keeps
 // each cell's top-k members by C (packed (ordered(C) << 32) | ~g keys) instead of weights;
 // the consistency and weights of those members are computed per cell by k_reduce_topk.
-template <typename DT, bool TOPK>
+template <typename DT, bool TOPK, bool TRACE>
 __global__ void __launch_bounds__(kThreads, kAssignBlocksPerSM)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m, TileIndex ti) {
@@ -742,7 +742,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   if (threadIdx.x == 0) { s_n = 0; s_ng = 0; }
   __syncthreads();
 
-  const bool trace = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
+  constexpr bool trace = TRACE;             // per-pixel trace (tests) in its own instantiation
   const float qnan = __int_as_float(0x7fc00000);
 
   // (a) Eq. 9 gate and compaction of the tile's gated pixels (any order: every reduction
@@ -1583,11 +1583,14 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                          cudaEvent_t* ev) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)assign_smem(kMaxK1));
+    const int sm = (int)assign_smem(kMaxK1);
+    cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assign<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)assign_smem(kMaxK1));
+      e = cudaFuncSetAttribute(k_assign<DT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_assign<DT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_assign<DT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1600,14 +1603,23 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                                                                        geo.count_chunks);
   k_levels<<<geo.emit_blocks, kThreads, 0, s>>>(t);
   mark(2);
+  const bool traced = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
   if (geo.top_k) {
-    k_assign<DT, true><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
-                                                                   (float)out.unit_m, geo.tiles);
+    if (traced)
+      k_assign<DT, true, true><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
+                                                                         (float)out.unit_m, geo.tiles);
+    else
+      k_assign<DT, true, false><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
+                                                                          (float)out.unit_m, geo.tiles);
     mark(3);
     k_reduce_topk<DT><<<geo.emit_blocks, kThreads, 0, s>>>(rig, rays, fp, t, out);
   } else {
-    k_assign<DT, false><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(rig, rays, fp, t, tr,
-                                                                               (float)out.unit_m, geo.tiles);
+    if (traced)
+      k_assign<DT, false, true><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(
+          rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
+    else
+      k_assign<DT, false, false><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(
+          rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
     mark(3);
     k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
   }
