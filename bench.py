@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson arrival trace of the served/plain comparison")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep fuseflow_create's launch geometry instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -220,6 +222,22 @@ def run_ours(args, rank, world, local_rank):
     sh = stream.cuda_stream
     FPS = args.frames_per_step
 
+    # launch geometry: the autotuner's choice on the pool's first frame (untimed set-up);
+    # results do not depend on it, so every context of this rig takes the same setting
+    tuning = {"autotuned": False, "chosen": ff.tuning()}
+    if not args.no_autotune:
+        d0 = dtensors[0]
+        tu, us0, us1 = ff.autotune(d0[0], d0[1], d0[2], reps=9, stream=sh)
+        tuning = {"autotuned": True, "chosen": tu.as_dict(), "start_frame_us": round(us0, 2),
+                  "chosen_frame_us": round(us1, 2),
+                  "method": "fuseflow_autotune: coordinate descent, median of 9 L2-flushed "
+                            "frames per candidate, kept when >= 1% faster"}
+
+    def tuned(ctx_obj):
+        g = tuning["chosen"]
+        ctx_obj.set_tuning(g["count_chunks"], g["emit_blocks"], g["prefetch_tiles"])
+        return ctx_obj
+
     def step():
         for i in range(FPS):
             t = dtensors[i % len(dtensors)]
@@ -255,12 +273,41 @@ def run_ours(args, rank, world, local_rank):
     value = job_rate(args.steps * FPS * px, world, ms)
     fps = job_rate(args.steps * FPS, world, ms)
 
+    # ------------------------------------------------------------ recorded fuse calls
+    # one CUDA graph per pool frame (fuseflow_graph_*: the memset and six kernels of a frame
+    # in one launch), replayed in the plain path's order on the same stream
+    graphs = [ff.graph(t[0], t[1], t[2]) for t in dtensors]
+
+    def graph_step():
+        for i in range(FPS):
+            F.fuseflow_graph_launch(graphs[i % len(graphs)].g, sh)
+
+    for _ in range(max(args.warmup, 1)):
+        graph_step()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    g0.record(stream)
+    for _ in range(args.steps):
+        graph_step()
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    gms = max_over_ranks(g0.elapsed_time(g1), world, dev)
+    gstatus, _ = ff.stats(sh, check=False)
+    for g in graphs:
+        g.close()
+    graph_line = {"value": round(job_rate(args.steps * FPS * px, world, gms), 1), "unit": "px/s",
+                  "frames_per_s": round(job_rate(args.steps * FPS, world, gms), 2),
+                  "ms_per_step": round(gms / args.steps, 4), "vs_plain": round(ms / gms, 4),
+                  "status_ok": gstatus == F.FUSEFLOW_OK,
+                  "path": "fuseflow_graph_launch, one recorded graph per pool frame"}
+
     # ------------------------------------------------------------ batched: frames in flight
     # the same frames through `slots` contexts on as many streams, frame k on slot k % slots
     batched = None
     if args.slots > 1:
         B = args.slots
-        ctxs = [ff] + [F.FuseFlow(rig) for _ in range(B - 1)]
+        ctxs = [ff] + [tuned(F.FuseFlow(rig)) for _ in range(B - 1)]
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(B - 1)]
 
         def batched_step():
@@ -306,6 +353,10 @@ def run_ours(args, rank, world, local_rank):
     top3 = None
     if True:
         ff3 = F.FuseFlow(rig, top_k=3)
+        if not args.no_autotune:
+            d0 = dtensors[0]
+            tu3, _, _ = ff3.autotune(d0[0], d0[1], d0[2], reps=9, stream=sh)
+            tuning["chosen_top3"] = tu3.as_dict()
 
         def top3_step():
             for i in range(FPS):
@@ -428,6 +479,8 @@ def run_ours(args, rank, world, local_rank):
     cap = ff.capacity
     srv = SV.Server(1 << 40)
     rid = srv.add_rig(rig, n_slots=B)
+    if not args.no_autotune:
+        srv.autotune(rid, pinned[0], reps=9)
     outs = deque(SV.HostCloud(cap) for _ in range(B + 1))
 
     def serve(n_frames):
@@ -494,13 +547,13 @@ def run_ours(args, rank, world, local_rank):
                    "pool_frames": len(pool), "pool_bytes": int(frame_bytes * len(pool)),
                    "l2": "inputs larger than L2: a pool of distinct frames is cycled, each frame "
                          "re-read only after the others",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "launch_geometry": tuning},
         "frames_per_s": round(fps, 2),
         "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5), "path": "plain, one frame per launch sequence"},
         "roofline": roof, "path_roofline": path_roof,
         "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "stage_roofline": stages,
-        "batched": batched, "top3_variant": top3, "serving": serving, "other_configs": configs,
+        "graph_replay": graph_line, "batched": batched, "top3_variant": top3, "serving": serving, "other_configs": configs,
         "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
         "cells_per_frame": int(n_cells), "status_ok": ok_status,
         "clocks": clocks, "cpu_baseline": cpu,
@@ -542,12 +595,15 @@ def run_configs(dev, frames_each: int = 64):
             dev_frames.append((d, c, r, [t.data_ptr() for t in d], [t.data_ptr() for t in c],
                                [t.data_ptr() for t in r]))
         ff = F.FuseFlow(rig)
+        t0_ = dev_frames[0]
+        tu, us0, us1 = ff.autotune(t0_[0], t0_[1], t0_[2], reps=9, stream=stream.cuda_stream)
         for i in range(4):
             t = dev_frames[i % len(dev_frames)]
             F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], stream.cuda_stream)
+        n_fr = frames_each if rig.n_pixels > (1 << 21) else 4 * frames_each   # small rigs: more
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(frames_each):
+        for i in range(n_fr):
             t = dev_frames[i % len(dev_frames)]
             F.fuseflow_fuse_frame(ff.ctx, t[3], t[4], t[5], stream.cuda_stream)
         e1.record(stream)
@@ -555,10 +611,25 @@ def run_configs(dev, frames_each: int = 64):
         ms = e0.elapsed_time(e1)
         status, st = ff.stats(stream.cuda_stream, check=False)
         px = rig.n_pixels
-        out[key] = {"cams": rig.n_cams, "px_per_frame": px, "frames_per_s": round(frames_each / (ms / 1e3), 2),
-                    "px_per_s": round(frames_each * px / (ms / 1e3), 1),
-                    "px_per_s_per_camera": round(frames_each * px / (ms / 1e3) / rig.n_cams, 1),
-                    "cells": int(st.n_cells), "status_ok": status == F.FUSEFLOW_OK}
+        # the same frames replayed from recorded graphs (one per distinct frame)
+        graphs = [ff.graph(t[0], t[1], t[2]) for t in dev_frames]
+        for i in range(4):
+            F.fuseflow_graph_launch(graphs[i % len(graphs)].g, stream.cuda_stream)
+        e0.record(stream)
+        for i in range(n_fr):
+            F.fuseflow_graph_launch(graphs[i % len(graphs)].g, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        gms = e0.elapsed_time(e1)
+        for g in graphs:
+            g.close()
+        out[key] = {"cams": rig.n_cams, "px_per_frame": px, "frames_per_s": round(n_fr / (ms / 1e3), 2),
+                    "px_per_s": round(n_fr * px / (ms / 1e3), 1),
+                    "px_per_s_per_camera": round(n_fr * px / (ms / 1e3) / rig.n_cams, 1),
+                    "cells": int(st.n_cells), "status_ok": status == F.FUSEFLOW_OK,
+                    "graph_frames_per_s": round(n_fr / (gms / 1e3), 2), "frames_timed": n_fr,
+                    "launch_geometry": dict(tu.as_dict(), start_frame_us=round(us0, 2),
+                                            chosen_frame_us=round(us1, 2))}
         ff.close()
     return out
 

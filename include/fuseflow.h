@@ -138,6 +138,22 @@ void fuseflow_destroy(fuseflow_ctx *ctx);
 int fuseflow_fuse_frame(fuseflow_ctx *ctx, const void *const *depth, const float *const *conf,
                         const uint8_t *const *rgb, fuseflow_cloud *out, void *stream);
 
+/* A fuse call recorded once as a CUDA graph, for callers whose input images live in the
+ * same device buffers every frame (a capture loop that refills them): replaying it with
+ * fuseflow_graph_launch is the same as calling fuseflow_fuse_frame with the pointers
+ * given here, whose contents may change between launches, at one launch instead of seven.
+ * The graph keeps the context's launch geometry and trace registration as they were at
+ * creation; results do not depend on the geometry.  It uses the context's tables, so
+ * launches of graphs and fuse calls of one context must be ordered (one stream), and
+ * every graph must be destroyed before its context.  create runs no GPU work (it records
+ * on a private stream of its own); it returns INVALID_ARG or CUDA. */
+typedef struct fuseflow_graph fuseflow_graph;
+int fuseflow_graph_create(fuseflow_ctx *ctx, const void *const *depth, const float *const *conf,
+                          const uint8_t *const *rgb, fuseflow_graph **out);
+/* Enqueues the recorded frame on `stream`; *out (may be NULL) as for fuseflow_fuse_frame. */
+int fuseflow_graph_launch(fuseflow_graph *graph, fuseflow_cloud *out, void *stream);
+void fuseflow_graph_destroy(fuseflow_graph *graph);
+
 /* Waits for `stream`, copies the last frame's statistics to *host_stats and returns
  * CAPACITY if the frame overflowed max_cells or a hash table, INTERNAL if a device-side
  * check failed, OK otherwise. */
@@ -204,6 +220,45 @@ int fuseflow_get_neighbours(const fuseflow_ctx *ctx, int32_t *out, int32_t *k_mi
 int fuseflow_enable_stage_timing(fuseflow_ctx *ctx, int enable);
 int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
 const char *fuseflow_stage_name(int stage);
+
+/* Launch geometry of a context: performance knobs only.  The fused cloud, its statistics
+ * and any trace are bitwise the same for every admissible setting (the path has no
+ * order-dependent arithmetic), so a setting can be chosen by timing alone.
+ *   count_chunks    2048-pixel chunks per block of the coarse-count step, 1..64
+ *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
+ *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
+ *                   depth rows into L2; 0 turns the prefetch off
+ * fuseflow_create picks count_chunks for one wave of three count blocks per SM,
+ * emit_blocks = 8 blocks per SM and prefetch_tiles = one wave of assign blocks. */
+typedef struct fuseflow_tuning {
+  int32_t count_chunks;
+  int32_t emit_blocks;
+  int32_t prefetch_tiles;
+  int32_t reserved;           /* 0 */
+} fuseflow_tuning;
+
+/* Reads (get) or replaces (set) the context's launch geometry.  set returns INVALID_ARG,
+ * leaving the context unchanged, for a value outside the ranges above.  Neither touches
+ * the GPU; set must not race with a fuse call of the same context still being enqueued
+ * from another host thread. */
+int fuseflow_get_tuning(const fuseflow_ctx *ctx, fuseflow_tuning *out);
+int fuseflow_set_tuning(fuseflow_ctx *ctx, const fuseflow_tuning *in);
+
+/* Autotuner of the launch geometry.  Fuses the given frame (DEVICE inputs as for
+ * fuseflow_fuse_frame) repeatedly on `stream` under candidate settings, one knob at a
+ * time (count_chunks, then emit_blocks, then prefetch_tiles; coordinate descent from
+ * the context's current setting), and keeps a candidate only when the median of `reps`
+ * timed frames (CUDA events on `stream`, L2 flushed before each frame by writing a
+ * scratch buffer of twice the L2 size) is at least 1 % below the best so far.  The
+ * chosen setting stays in the context and is copied to *chosen (may be NULL);
+ * frame_us[0] and frame_us[1] (may be NULL) receive the median frame time, in
+ * microseconds, of the starting and of the chosen setting, both measured at the end.
+ * Any trace registered with fuseflow_set_trace is suspended while tuning.  Synchronous:
+ * returns after `stream` is idle; the context's outputs then hold the frame's cloud.
+ * reps in 3..101.  Returns INVALID_ARG, OUT_OF_MEMORY (scratch), CUDA. */
+int fuseflow_autotune(fuseflow_ctx *ctx, const void *const *depth, const float *const *conf,
+                      const uint8_t *const *rgb, int32_t reps, fuseflow_tuning *chosen,
+                      double *frame_us, void *stream);
 
 /* Number of pixels of the rig (sum of W_i H_i) and the output capacity. */
 int64_t fuseflow_num_pixels(const fuseflow_ctx *ctx);
@@ -308,6 +363,15 @@ int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_
 
 /* Frames submitted but not yet reported by fuseflow_server_poll. */
 int64_t fuseflow_server_pending(const fuseflow_server *srv);
+
+/* Autotunes the launch geometry of rig `rig` (fuseflow_autotune on the context of its
+ * first slot, with one sample frame given as HOST pointers as for submit) and applies the
+ * chosen setting to all of the rig's slots.  The rig must be idle: INVALID_ARG while any
+ * of its frames is in flight or waiting.  Synchronous.  *chosen and frame_us as for
+ * fuseflow_autotune (either may be NULL). */
+int fuseflow_server_autotune(fuseflow_server *srv, int32_t rig, const void *const *depth,
+                             const float *const *conf, const uint8_t *const *rgb,
+                             int32_t reps, fuseflow_tuning *chosen, double *frame_us);
 
 /* Device bytes held by the server's slots (<= the budget). */
 int64_t fuseflow_server_device_bytes(const fuseflow_server *srv);

@@ -39,6 +39,8 @@ struct fuseflow_ctx {
   size_t out_bytes = 0;
   TraceDev trace{};
   Geometry geo{};
+  long long max_chunks = 0;            // 2048-pixel chunks of the largest camera
+  int bstats_cap = 0;                  // count-step block statistics allocated (chunks = 1)
   // staging for the host-buffer entry point
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -48,6 +50,13 @@ struct fuseflow_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> events;     // kTimingRing * (FUSEFLOW_N_STAGES + 1)
   long long timed_frames = 0;
+};
+
+// One fuse call captured as a CUDA graph (the memset and kernels of launch_frame).
+struct fuseflow_graph {
+  fuseflow_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 static constexpr int kTimingRing = 1024;
@@ -334,8 +343,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 2047) / 2048;
     const long long per = (total_chunks + 3ll * sms - 1) / (3ll * sms);
     ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
-    const long long max_chunks = (max_px + 2047) / 2048;
-    ctx->geo.count_blocks_x = (int)((max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
+    ctx->max_chunks = (max_px + 2047) / 2048;
+    ctx->geo.count_blocks_x = (int)((ctx->max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
   ctx->geo.emit_blocks = std::max(1, sms * 8);
 
@@ -343,6 +352,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   int status = FUSEFLOW_OK;
   const long long n_words = (off + 31) / 32;
   const int n_wblocks = (int)((n_words + 1023) / 1024);
+  // block statistics for the finest count geometry a tuning may choose (one chunk a block)
+  ctx->bstats_cap = (int)(ctx->max_chunks * n_cams);
   const int n_bstats = ctx->geo.count_blocks_x * n_cams;
   size_t o = 0;
   auto take = [&](size_t bytes, size_t align) { o = align_up(o, align); size_t at = o; o += bytes; return at; };
@@ -353,7 +364,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const size_t o_coarse = take(sizeof(CoarseEntry) * ctx->ccap, 256);
   const size_t o_cused = take(sizeof(unsigned) * ctx->ccap, 256);
   const size_t o_cnt = take(sizeof(FrameCounters) + sizeof(unsigned) * (size_t)n_words, 256);
-  const size_t o_bst = take(sizeof(BlockStats) * (size_t)n_bstats, 256);
+  const size_t o_bst = take(sizeof(BlockStats) * (size_t)ctx->bstats_cap, 256);
   const size_t o_part = take(sizeof(Partial) * (size_t)max_partials, 256);
   const size_t o_staged = take(sizeof(CellOut) * (size_t)ctx->max_cells, 256);
   const size_t o_wpre = take(sizeof(unsigned) * (size_t)n_words, 256);
@@ -430,6 +441,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
         cudaMemset(ctx->d_tables, 0, ctx->table_bytes) != cudaSuccess ||
         cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
         launch_init_tables(t, ctx->max_slots, ctx->ccap, 0) != cudaSuccess ||
+        prepare_launch(rig->depth_f32 != 0) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
       status = FUSEFLOW_ERR_CUDA;
   }
@@ -483,6 +495,55 @@ int fuseflow_fuse_frame(fuseflow_ctx* ctx, const void* const* depth, const float
   if (e != cudaSuccess) return FUSEFLOW_ERR_CUDA;
   if (out) fill_cloud(ctx, out);
   return FUSEFLOW_OK;
+}
+
+int fuseflow_graph_create(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                          const uint8_t* const* rgb, fuseflow_graph** out) {
+  if (!ctx || !out) return FUSEFLOW_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ok = 0;
+  const FramePtrs fp = frame_ptrs(ctx, depth, conf, rgb, &ok);
+  if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
+  fuseflow_graph* g = new (std::nothrow) fuseflow_graph();
+  if (!g) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  g->ctx = ctx;
+  cudaStream_t s = nullptr;
+  int st = FUSEFLOW_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    s = nullptr;
+    st = FUSEFLOW_ERR_CUDA;
+  } else if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    st = FUSEFLOW_ERR_CUDA;
+  } else {
+    const cudaError_t e = launch_frame(ctx->d_rig, ctx->d_rays, fp, ctx->tab, ctx->trace, ctx->out,
+                                       ctx->geo, s, nullptr);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g->graph ||
+        cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+      st = FUSEFLOW_ERR_CUDA;
+  }
+  if (s) cudaStreamDestroy(s);
+  if (st != FUSEFLOW_OK) {
+    cudaGetLastError();
+    fuseflow_graph_destroy(g);
+    return st;
+  }
+  *out = g;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_graph_launch(fuseflow_graph* g, fuseflow_cloud* out, void* stream) {
+  if (!g || !g->exec) return FUSEFLOW_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+  if (out) fill_cloud(g->ctx, out);
+  return FUSEFLOW_OK;
+}
+
+void fuseflow_graph_destroy(fuseflow_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 int fuseflow_read_stats(fuseflow_ctx* ctx, fuseflow_stats* host_stats, void* stream) {
@@ -672,6 +733,149 @@ int fuseflow_read_stage_times(fuseflow_ctx* ctx, double* ms, int64_t* n_frames) 
     }
   }
   ctx->timed_frames = 0;
+  return FUSEFLOW_OK;
+}
+
+// Launch geometry from a (validated) tuning: the count step's grid follows its chunks per
+// block, and the scan step reads exactly the block statistics that grid writes.
+static void apply_tuning(fuseflow_ctx* ctx, const fuseflow_tuning& tu) {
+  ctx->geo.count_chunks = tu.count_chunks;
+  ctx->geo.count_blocks_x = (int)((ctx->max_chunks + tu.count_chunks - 1) / tu.count_chunks);
+  ctx->tab.n_bstats = ctx->geo.count_blocks_x * ctx->n_cams;
+  ctx->geo.emit_blocks = tu.emit_blocks;
+  ctx->geo.tiles.ahead = tu.prefetch_tiles == 0 ? kNoPrefetch : std::min(tu.prefetch_tiles, kNoPrefetch);
+}
+
+// Coordinate descent over the launch geometry, timing whole frames on one stream.
+struct Autotuner {
+  fuseflow_ctx* ctx;
+  FramePtrs fp;
+  int reps;
+  cudaStream_t s;
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  std::vector<cudaEvent_t> ev;
+  double start_us = 0.0, best_us = 0.0;
+
+  Autotuner(fuseflow_ctx* c, const FramePtrs& f, int r, cudaStream_t st) : ctx(c), fp(f), reps(r), s(st) {}
+  ~Autotuner() {
+    if (flush) cudaFree(flush);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+
+  // Median frame time (us) of the context's current geometry.
+  int measure(double* us) {
+    std::vector<float> t((size_t)reps);
+    for (int r = -1; r < reps; ++r) {                 // one untimed frame first
+      if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s) != cudaSuccess ||
+          cudaEventRecord(ev[2 * std::max(r, 0)], s) != cudaSuccess ||
+          launch_frame(ctx->d_rig, ctx->d_rays, fp, ctx->tab, TraceDev{}, ctx->out, ctx->geo, s, nullptr) !=
+              cudaSuccess ||
+          cudaEventRecord(ev[2 * std::max(r, 0) + 1], s) != cudaSuccess)
+        return FUSEFLOW_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+    for (int r = 0; r < reps; ++r)
+      if (cudaEventElapsedTime(&t[(size_t)r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+    *us = 1e3 * t[(size_t)(reps / 2)];
+    return FUSEFLOW_OK;
+  }
+
+  int time_setting(const fuseflow_tuning& tu, double* us) {
+    apply_tuning(ctx, tu);
+    return measure(us);
+  }
+
+  int run() {
+    int dev = 0, l2 = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+    flush_bytes = 2 * (size_t)std::max(l2, 1 << 20);
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+      flush = nullptr;
+      cudaGetLastError();
+      return FUSEFLOW_ERR_OUT_OF_MEMORY;
+    }
+    ev.resize(2 * (size_t)reps);
+    for (cudaEvent_t& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return FUSEFLOW_ERR_CUDA; }
+
+    fuseflow_tuning start{};
+    fuseflow_get_tuning(ctx, &start);
+    fuseflow_tuning best = start;
+    int st = time_setting(best, &best_us);
+    if (st != FUSEFLOW_OK) return st;
+    auto consider = [&](fuseflow_tuning cand) -> int {
+      if (std::memcmp(&cand, &best, sizeof cand) == 0) return FUSEFLOW_OK;
+      double us = 0.0;
+      const int r = time_setting(cand, &us);
+      if (r == FUSEFLOW_OK && us < 0.99 * best_us) { best = cand; best_us = us; }
+      return r;
+    };
+    // count_chunks: one wave of b count blocks per SM, for b in 1..8
+    long long total_chunks = 0;
+    for (int i = 0; i < ctx->n_cams; ++i)
+      total_chunks += ((long long)ctx->intr[i].width * ctx->intr[i].height + 2047) / 2048;
+    for (int b : {1, 2, 3, 4, 6, 8}) {
+      fuseflow_tuning c = best;
+      const long long per = (total_chunks + (long long)b * sms - 1) / ((long long)b * sms);
+      c.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
+      if ((st = consider(c)) != FUSEFLOW_OK) return st;
+    }
+    for (int b : {1, 2, 4, 8, 16}) {
+      fuseflow_tuning c = best;
+      c.emit_blocks = b * sms;
+      if ((st = consider(c)) != FUSEFLOW_OK) return st;
+    }
+    const int wave = assign_resident_blocks() * sms;
+    for (int a : {0, wave / 2, wave, 2 * wave}) {
+      fuseflow_tuning c = best;
+      c.prefetch_tiles = a;
+      if ((st = consider(c)) != FUSEFLOW_OK) return st;
+    }
+    // both settings timed again back to back, so that clocks drift into neither
+    if ((st = time_setting(start, &start_us)) != FUSEFLOW_OK) return st;
+    if ((st = time_setting(best, &best_us)) != FUSEFLOW_OK) return st;
+    if (start_us <= best_us) {             // no gain after all: keep the caller's setting
+      apply_tuning(ctx, start);
+      best_us = start_us;
+    }
+    return FUSEFLOW_OK;
+  }
+};
+
+int fuseflow_get_tuning(const fuseflow_ctx* ctx, fuseflow_tuning* out) {
+  if (!ctx || !out) return FUSEFLOW_ERR_INVALID_ARG;
+  out->count_chunks = ctx->geo.count_chunks;
+  out->emit_blocks = ctx->geo.emit_blocks;
+  out->prefetch_tiles = ctx->geo.tiles.ahead >= kNoPrefetch ? 0 : ctx->geo.tiles.ahead;
+  out->reserved = 0;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_set_tuning(fuseflow_ctx* ctx, const fuseflow_tuning* in) {
+  if (!ctx || !in || in->count_chunks < 1 || in->count_chunks > 64 || in->emit_blocks < 1 ||
+      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || in->reserved != 0)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  apply_tuning(ctx, *in);
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_autotune(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                      const uint8_t* const* rgb, int32_t reps, fuseflow_tuning* chosen,
+                      double* frame_us, void* stream) {
+  if (!ctx || reps < 3 || reps > 101) return FUSEFLOW_ERR_INVALID_ARG;
+  int ok = 0;
+  const FramePtrs fp = frame_ptrs(ctx, depth, conf, rgb, &ok);
+  if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
+  Autotuner at(ctx, fp, reps, static_cast<cudaStream_t>(stream));
+  const int st = at.run();
+  if (st != FUSEFLOW_OK) return st;
+  if (chosen) fuseflow_get_tuning(ctx, chosen);
+  if (frame_us) { frame_us[0] = at.start_us; frame_us[1] = at.best_us; }
   return FUSEFLOW_OK;
 }
 

@@ -63,6 +63,9 @@ struct OutDev {
   double unit_m;                 // metres per depth unit
 };
 
+// Assign-step prefetch distance (tiles) that turns the L2 prefetch off.
+constexpr int kNoPrefetch = 1 << 30;
+
 struct Geometry {
   int n_cams;
   int depth_f32;
@@ -125,6 +128,9 @@ cudaError_t launch_confidence(const ConfArgs& a, bool depth_f32, int max_w, int 
 int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
 int fill_tile_index(const RigDev& rig, TileIndex* out);
 void fill_block_consts(const RigDev& rig, BlockConst* out);
+// Kernel attributes a frame's launches need (called by context creation, so that a later
+// stream capture of launch_frame makes no attribute call).
+cudaError_t prepare_launch(bool depth_f32);
 // ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp,
                          const Tables& t, const TraceDev& tr, const OutDev& out,

@@ -1577,23 +1577,30 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   }
 }
 
+// Dynamic shared memory limit of the assign kernels for one depth type, set once (the
+// first call comes from context creation, outside any stream capture).
+template <typename DT>
+cudaError_t set_assign_attributes() {
+  static bool attr_set = false;
+  if (attr_set) return cudaSuccess;
+  const int sm = (int)assign_smem(kMaxK1);
+  cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_assign<DT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_assign<DT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_assign<DT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) attr_set = true;
+  return e;
+}
+
 template <typename DT>
 cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
                          const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
                          cudaEvent_t* ev) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const int sm = (int)assign_smem(kMaxK1);
-    cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assign<DT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assign<DT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assign<DT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const cudaError_t ae = set_assign_attributes<DT>();
+  if (ae != cudaSuccess) return ae;
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
   cudaError_t err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
@@ -1653,7 +1660,7 @@ int fill_tile_index(const RigDev& rig, TileIndex* out) {
   for (int i = 1; i < rig.n_cams; ++i)
     same = same && rig.cam[i].W == rig.cam[0].W && rig.cam[i].H == rig.cam[0].H;
   out->per_cam = same && rig.n_cams > 0 ? out->first[1] : 0;
-  out->ahead = 1 << 30;                          // no prefetch unless the caller sets it
+  out->ahead = kNoPrefetch;                      // no prefetch unless the caller sets it
   return n;
 }
 
@@ -1698,6 +1705,10 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
   if (depth_f32) k_mc<float><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
   else k_mc<uint16_t><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_launch(bool depth_f32) {
+  return depth_f32 ? set_assign_attributes<float>() : set_assign_attributes<uint16_t>();
 }
 
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,

@@ -1,7 +1,7 @@
 // Serving runtime of the FUSE-Flow fusion path: several rigs resident on one GPU, frames
 // from host memory, continuous batching over per-rig frame slots (declared in
-// include/fuseflow.h).  Host code only; the per-frame work is fuseflow_fuse_frame on the
-// slot's own context plus the copy-out kernel.
+// include/fuseflow.h).  Host code only; the per-frame work is the slot's recorded fuse
+// call (a CUDA graph over its staging buffer) plus the copy-out kernel.
 #include <algorithm>
 #include <deque>
 #include <new>
@@ -23,6 +23,7 @@ struct Request {
 
 struct Slot {
   fuseflow_ctx* ctx = nullptr;
+  fuseflow_graph* graph = nullptr;      // the fuse call on d_in, recorded once
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   char* d_in = nullptr;                 // input staging: per camera depth | conf | rgb
@@ -45,6 +46,7 @@ size_t round256(size_t v) { return (v + 255) / 256 * 256; }
 
 void release_slot(Slot& s) {
   if (s.stream) cudaStreamSynchronize(s.stream);
+  if (s.graph) fuseflow_graph_destroy(s.graph);
   if (s.ctx) fuseflow_destroy(s.ctx);
   if (s.d_in) cudaFree(s.d_in);
   if (s.h_stats) cudaFreeHost(s.h_stats);
@@ -90,31 +92,63 @@ int map_outputs(const fuseflow_host_cloud& o, fuseflow_stats* h_stats, HostOutDe
   return FUSEFLOW_OK;
 }
 
+// Device copies of one frame's images in slot s's staging buffer.
+struct Staged {
+  std::vector<const void*> depth;
+  std::vector<const float*> conf;
+  std::vector<const uint8_t*> rgb;
+};
+
+// Per camera depth | conf | rgb in slot s's staging buffer.
+Staged staging(const Rig& g, const Slot& s) {
+  Staged out;
+  size_t o = 0;
+  for (int i = 0; i < g.n_cams; ++i) {
+    const size_t px = g.px[i];
+    out.depth.push_back(s.d_in + o); o += round256(px * g.depth_bytes);
+    out.conf.push_back(reinterpret_cast<const float*>(s.d_in + o)); o += round256(px * 4);
+    out.rgb.push_back(reinterpret_cast<const uint8_t*>(s.d_in + o)); o += round256(px * 3);
+  }
+  return out;
+}
+
+// Enqueues the host-to-device copies of a frame's images (host pointers per camera) into
+// slot s's staging buffer on its stream.
+int stage(const Rig& g, const Slot& s, const void* const* depth, const float* const* conf,
+          const uint8_t* const* rgb) {
+  const Staged in = staging(g, s);
+  for (int i = 0; i < g.n_cams; ++i) {
+    const size_t px = g.px[i];
+    if (cudaMemcpyAsync(const_cast<void*>(in.depth[i]), depth[i], px * g.depth_bytes, cudaMemcpyHostToDevice,
+                        s.stream) != cudaSuccess ||
+        cudaMemcpyAsync(const_cast<float*>(in.conf[i]), conf[i], px * 4, cudaMemcpyHostToDevice, s.stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(const_cast<uint8_t*>(in.rgb[i]), rgb[i], px * 3, cudaMemcpyHostToDevice, s.stream) !=
+            cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+  }
+  return FUSEFLOW_OK;
+}
+
+// (Re-)records slot s's fuse call on its staging buffer as a graph (after any change of the
+// context's launch geometry, so that the replay uses the current one).
+int record(const Rig& g, Slot& s) {
+  if (s.graph) fuseflow_graph_destroy(s.graph);
+  s.graph = nullptr;
+  const Staged in = staging(g, s);
+  return fuseflow_graph_create(s.ctx, in.depth.data(), in.conf.data(), in.rgb.data(), &s.graph);
+}
+
 // Enqueues request r on free slot s of rig g: host-to-device copies of the images, the
 // fusion kernels, the copy-out into the caller's host arrays, then the slot's event.
 int start(Rig& g, Slot& s, const Request& r) {
   HostOutDev hd{};
   int st = map_outputs(r.out, s.h_stats, &hd);
   if (st != FUSEFLOW_OK) return st;
-  std::vector<const void*> dp(g.n_cams);
-  std::vector<const float*> cp(g.n_cams);
-  std::vector<const uint8_t*> rp(g.n_cams);
-  size_t o = 0;
-  for (int i = 0; i < g.n_cams; ++i) {
-    const size_t px = g.px[i];
-    char* d = s.d_in + o; o += round256(px * g.depth_bytes);
-    char* c = s.d_in + o; o += round256(px * 4);
-    char* b = s.d_in + o; o += round256(px * 3);
-    if (cudaMemcpyAsync(d, r.depth[i], px * g.depth_bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-        cudaMemcpyAsync(c, r.conf[i], px * 4, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-        cudaMemcpyAsync(b, r.rgb[i], px * 3, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
-      return FUSEFLOW_ERR_CUDA;
-    dp[i] = d;
-    cp[i] = reinterpret_cast<const float*>(c);
-    rp[i] = reinterpret_cast<const uint8_t*>(b);
-  }
+  st = stage(g, s, r.depth.data(), r.conf.data(), r.rgb.data());
+  if (st != FUSEFLOW_OK) return st;
   fuseflow_cloud cl;
-  st = fuseflow_fuse_frame(s.ctx, dp.data(), cp.data(), rp.data(), &cl, s.stream);
+  st = fuseflow_graph_launch(s.graph, &cl, s.stream);
   if (st != FUSEFLOW_OK) return st;
   if (launch_copyout(cl, hd, s.stream) != cudaSuccess ||
       cudaEventRecord(s.done, s.stream) != cudaSuccess)
@@ -184,6 +218,10 @@ int fuseflow_server_add_rig(fuseflow_server* srv, const fuseflow_intrinsics* int
       cudaGetLastError();
       release_slot(s);
       st = FUSEFLOW_ERR_CUDA;
+      break;
+    }
+    if ((st = record(g, s)) != FUSEFLOW_OK) {
+      release_slot(s);
       break;
     }
     added += bytes;
@@ -259,6 +297,33 @@ int fuseflow_server_poll(fuseflow_server* srv, fuseflow_completion* done, int32_
     }
   }
   return status;
+}
+
+int fuseflow_server_autotune(fuseflow_server* srv, int32_t rig, const void* const* depth,
+                             const float* const* conf, const uint8_t* const* rgb, int32_t reps,
+                             fuseflow_tuning* chosen, double* frame_us) {
+  if (!srv || rig < 0 || rig >= (int32_t)srv->rigs.size() || !depth || !conf || !rgb)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  Rig& g = srv->rigs[rig];
+  if (!g.waiting.empty()) return FUSEFLOW_ERR_INVALID_ARG;
+  for (const Slot& s : g.slots)
+    if (s.busy) return FUSEFLOW_ERR_INVALID_ARG;
+  for (int i = 0; i < g.n_cams; ++i)
+    if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
+  Slot& s = g.slots[0];
+  int st = stage(g, s, depth, conf, rgb);
+  if (st != FUSEFLOW_OK) return st;
+  const Staged in = staging(g, s);
+  fuseflow_tuning tu{};
+  st = fuseflow_autotune(s.ctx, in.depth.data(), in.conf.data(), in.rgb.data(), reps, &tu, frame_us,
+                         s.stream);
+  if (st != FUSEFLOW_OK) return st;
+  for (Slot& o : g.slots) {
+    fuseflow_set_tuning(o.ctx, &tu);
+    if ((st = record(g, o)) != FUSEFLOW_OK) return st;
+  }
+  if (chosen) *chosen = tu;
+  return FUSEFLOW_OK;
 }
 
 int64_t fuseflow_server_pending(const fuseflow_server* srv) { return srv ? srv->pending : 0; }

@@ -77,6 +77,15 @@ class fuseflow_host_cloud(C.Structure):
                 ("capacity", C.c_int64)]
 
 
+class fuseflow_tuning(C.Structure):
+    _fields_ = [("count_chunks", C.c_int32), ("emit_blocks", C.c_int32),
+                ("prefetch_tiles", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"count_chunks": self.count_chunks, "emit_blocks": self.emit_blocks,
+                "prefetch_tiles": self.prefetch_tiles}
+
+
 class fuseflow_completion(C.Structure):
     _fields_ = [("request", C.c_int64), ("rig", C.c_int32), ("status", C.c_int32),
                 ("stats", fuseflow_stats)]
@@ -89,6 +98,10 @@ EXPORTS = {
     "fuseflow_destroy": (None, [C.c_void_p]),
     "fuseflow_fuse_frame": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), C.POINTER(fuseflow_cloud), C.c_void_p]),
+    "fuseflow_graph_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "fuseflow_graph_launch": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_cloud), C.c_void_p]),
+    "fuseflow_graph_destroy": (None, [C.c_void_p]),
     "fuseflow_read_stats": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_stats), C.c_void_p]),
     "fuseflow_fuse_frame_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                            C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -115,6 +128,15 @@ EXPORTS = {
     "fuseflow_mc_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p),
                                     C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.c_void_p]),
+    "fuseflow_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_tuning)]),
+    "fuseflow_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_tuning)]),
+    "fuseflow_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p), C.c_int32, C.POINTER(fuseflow_tuning),
+                                    C.POINTER(C.c_double), C.c_void_p]),
+    "fuseflow_server_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                           C.c_int32, C.POINTER(fuseflow_tuning),
+                                           C.POINTER(C.c_double)]),
     "fuseflow_server_create": (C.c_int, [C.c_int64, C.POINTER(C.c_void_p)]),
     "fuseflow_server_add_rig": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_intrinsics),
                                           C.POINTER(fuseflow_extrinsics), C.c_int32,
@@ -212,6 +234,24 @@ def fuseflow_fuse_frame(ctx, depth_ptrs, conf_ptrs, rgb_ptrs, stream: int = 0) -
                                       _ptr_array(rgb_ptrs), C.byref(cloud), C.c_void_p(stream)),
            "fuseflow_fuse_frame")
     return cloud
+
+
+def fuseflow_graph_create(ctx, depth_ptrs, conf_ptrs, rgb_ptrs) -> C.c_void_p:
+    g = C.c_void_p()
+    _check(load().fuseflow_graph_create(ctx, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                        _ptr_array(rgb_ptrs), C.byref(g)), "fuseflow_graph_create")
+    return g
+
+
+def fuseflow_graph_launch(graph, stream: int = 0) -> fuseflow_cloud:
+    cloud = fuseflow_cloud()
+    _check(load().fuseflow_graph_launch(graph, C.byref(cloud), C.c_void_p(stream)),
+           "fuseflow_graph_launch")
+    return cloud
+
+
+def fuseflow_graph_destroy(graph) -> None:
+    load().fuseflow_graph_destroy(graph)
 
 
 def fuseflow_read_stats(ctx, stream: int = 0, check: bool = True):
@@ -316,6 +356,38 @@ def fuseflow_mc_error(ctx, pos_ptr: int, n_points: int, depth_ptrs, err_ptr: int
                                     C.byref(mc),
                                     C.byref(used), C.c_void_p(stream)), "fuseflow_mc_error")
     return mc.value, used.value
+
+
+def fuseflow_get_tuning(ctx) -> fuseflow_tuning:
+    tu = fuseflow_tuning()
+    _check(load().fuseflow_get_tuning(ctx, C.byref(tu)), "fuseflow_get_tuning")
+    return tu
+
+
+def fuseflow_set_tuning(ctx, count_chunks: int, emit_blocks: int, prefetch_tiles: int) -> int:
+    """Status of replacing the context's launch geometry (INVALID_ARG leaves it unchanged)."""
+    tu = fuseflow_tuning(count_chunks, emit_blocks, prefetch_tiles, 0)
+    return load().fuseflow_set_tuning(ctx, C.byref(tu))
+
+
+def fuseflow_autotune(ctx, depth_ptrs, conf_ptrs, rgb_ptrs, reps: int = 9, stream: int = 0):
+    """(chosen fuseflow_tuning, median frame us before, after) for one device frame."""
+    tu = fuseflow_tuning()
+    us = (C.c_double * 2)()
+    _check(load().fuseflow_autotune(ctx, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                    _ptr_array(rgb_ptrs), reps, C.byref(tu), us,
+                                    C.c_void_p(stream)), "fuseflow_autotune")
+    return tu, us[0], us[1]
+
+
+def fuseflow_server_autotune(srv, rig: int, depth_ptrs, conf_ptrs, rgb_ptrs, reps: int = 9):
+    """As fuseflow_autotune for all slots of an idle served rig (HOST frame pointers)."""
+    tu = fuseflow_tuning()
+    us = (C.c_double * 2)()
+    _check(load().fuseflow_server_autotune(srv, rig, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                           _ptr_array(rgb_ptrs), reps, C.byref(tu), us),
+           "fuseflow_server_autotune")
+    return tu, us[0], us[1]
 
 
 def fuseflow_server_create(hbm_budget_bytes: int) -> C.c_void_p:
@@ -434,9 +506,57 @@ class FuseFlow:
                 "rep": device_view(cloud.rep, (n,), "<i4"),
                 "key": device_view(cloud.key, (n,), "<i8")}
 
+    def autotune(self, depth, conf, rgb, reps: int = 9, stream: Optional[int] = None):
+        """Tunes the launch geometry on one frame of CUDA tensors: (tuning, us before, after)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_autotune(self.ctx, [t.data_ptr() for t in depth],
+                                 [t.data_ptr() for t in conf], [t.data_ptr() for t in rgb],
+                                 reps, stream)
+
+    def graph(self, depth, conf, rgb) -> "FrameGraph":
+        """The fuse call on these CUDA tensors recorded once, for replay (the tensors are
+        read at every launch; keep them alive while the graph is used)."""
+        return FrameGraph(self, depth, conf, rgb)
+
+    def tuning(self) -> dict:
+        return fuseflow_get_tuning(self.ctx).as_dict()
+
+    def set_tuning(self, count_chunks: int, emit_blocks: int, prefetch_tiles: int):
+        _check(fuseflow_set_tuning(self.ctx, count_chunks, emit_blocks, prefetch_tiles),
+               "fuseflow_set_tuning")
+
     def set_trace(self, **arrays):
         fuseflow_set_trace(self.ctx, **{k: (v.data_ptr() if v is not None else 0)
                                         for k, v in arrays.items()})
 
     def clear_trace(self):
         fuseflow_set_trace(self.ctx, clear=True)
+
+
+class FrameGraph:
+    """A recorded fuse call of one context (fuseflow_graph_*)."""
+
+    def __init__(self, ff: "FuseFlow", depth, conf, rgb):
+        self.ff = ff
+        self.inputs = (list(depth), list(conf), list(rgb))
+        self.g = fuseflow_graph_create(ff.ctx, [t.data_ptr() for t in depth],
+                                       [t.data_ptr() for t in conf], [t.data_ptr() for t in rgb])
+
+    def launch(self, stream: Optional[int] = None) -> fuseflow_cloud:
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_graph_launch(self.g, stream)
+
+    def close(self):
+        if self.g:
+            fuseflow_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

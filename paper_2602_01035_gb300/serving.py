@@ -92,6 +92,11 @@ class Server:
         return F.fuseflow_server_submit(self.srv, rid, frame["depth"], frame["conf"],
                                         frame["rgb"], out.c)
 
+    def autotune(self, rid: int, frame: dict, reps: int = 9):
+        """Launch geometry of an idle rig tuned on one pinned frame: (tuning, us before, after)."""
+        return F.fuseflow_server_autotune(self.srv, rid, frame["depth"], frame["conf"],
+                                          frame["rgb"], reps)
+
     def poll(self):
         n = F.fuseflow_server_poll(self.srv, self._done, len(self._done))
         return [(self._done[i].request, self._done[i].rig, self._done[i].status,

@@ -129,3 +129,23 @@ def test_server_rejects_bad_arguments_without_a_gpu(ffmod):
     assert lib.fuseflow_server_pending(None) == 0
     assert lib.fuseflow_server_device_bytes(None) == 0
     lib.fuseflow_server_destroy(None)
+
+
+def test_tuning_entry_points_reject_bad_arguments_without_a_gpu(ffmod):
+    lib = ffmod.load()
+    tu = ffmod.fuseflow_tuning(4, 1216, 608, 0)
+    bad = ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_get_tuning(None, C.byref(tu)) == bad
+    assert lib.fuseflow_set_tuning(None, C.byref(tu)) == bad
+    us = (C.c_double * 2)()
+    assert lib.fuseflow_autotune(None, None, None, None, 9, C.byref(tu), us, None) == bad
+    assert lib.fuseflow_server_autotune(None, 0, None, None, None, 9, C.byref(tu), us) == bad
+
+
+def test_graph_entry_points_reject_bad_arguments_without_a_gpu(ffmod):
+    lib = ffmod.load()
+    g = C.c_void_p()
+    bad = ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_graph_create(None, None, None, None, C.byref(g)) == bad
+    assert lib.fuseflow_graph_launch(None, None, None) == bad
+    lib.fuseflow_graph_destroy(None)

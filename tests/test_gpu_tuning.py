@@ -1,0 +1,141 @@
+"""Launch-geometry tuning (fuseflow_get/set_tuning, fuseflow_autotune, and the server's
+autotune): every admissible setting gives bitwise the same cloud, statistics and trace,
+out-of-range settings are refused without effect, and the autotuner keeps a setting no
+slower than the one it started from."""
+import numpy as np
+import pytest
+
+from paper_2602_01035_gb300 import scenes as S
+from parity import run_gpu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# (count_chunks, emit_blocks, prefetch_tiles): the extremes of each range and a few between
+SETTINGS = [(1, 1, 0), (64, 65536, 1), (2, 152, 304), (7, 999, 1 << 20), (64, 3, 0)]
+
+
+@pytest.fixture(scope="module")
+def ffmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_01035_gb300 import fuseflow
+    fuseflow.load()
+    return fuseflow
+
+
+def _same(a, b, with_trace=True):
+    assert a["status"] == b["status"]
+    assert a["stats"] == b["stats"]
+    for k in ("pos", "rgb", "weight", "count", "rep", "key"):
+        assert np.array_equal(a["cells"][k], b["cells"][k], equal_nan=True), k
+    if with_trace:
+        for k in a["trace"]:
+            assert np.array_equal(a["trace"][k], b["trace"][k], equal_nan=True), k
+
+
+def _cases():
+    r1, _, f1 = S.config1()
+    r2 = S.tiny_rig(n=3, width=97, height=61, spread_deg=25.0, fx=80.0, fy=78.0)
+    f2 = S.random_frame(r2, seed=41, zero_frac=0.03, flying_frac=0.01)
+    r3, _, f3 = S.config3(frame=2)
+    return [("config1", r1, f1), ("ragged", r2, f2), ("8x1280x720", r3, f3)]
+
+
+@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("top_k", [0, 3])
+def test_every_setting_gives_the_same_result(ffmod, case, top_k):
+    name, rig, fr = _cases()[case]
+    ff = ffmod.FuseFlow(rig, top_k=top_k)
+    try:
+        trace = name != "8x1280x720"
+        base = run_gpu(ff, fr, torch, with_trace=trace)
+        assert base["stats"]["n_cells"] > 0
+        for cc, eb, pf in SETTINGS:
+            ff.set_tuning(cc, eb, pf)
+            assert ff.tuning() == {"count_chunks": cc, "emit_blocks": eb, "prefetch_tiles": pf}
+            _same(base, run_gpu(ff, fr, torch, with_trace=trace), with_trace=trace)
+    finally:
+        ff.close()
+
+
+def test_out_of_range_settings_are_refused_without_effect(ffmod):
+    rig, _, _ = S.config1()
+    ff = ffmod.FuseFlow(rig)
+    try:
+        before = ff.tuning()
+        assert before["count_chunks"] >= 1 and before["emit_blocks"] >= 1
+        for cc, eb, pf in [(0, 8, 0), (65, 8, 0), (1, 0, 0), (1, 65537, 0), (1, 8, -1)]:
+            assert ffmod.fuseflow_set_tuning(ff.ctx, cc, eb, pf) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+            assert ff.tuning() == before
+    finally:
+        ff.close()
+
+
+def test_autotune_keeps_the_result_and_a_setting_no_slower(ffmod):
+    rig, _, fr = S.config3(frame=4)
+    ff = ffmod.FuseFlow(rig)
+    dev = torch.device("cuda")
+    try:
+        base = run_gpu(ff, fr, torch, with_trace=False)
+        d = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.depth]
+        c = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.conf]
+        r = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.rgb]
+        # a registered trace is not written while tuning
+        sentinel = torch.full((ff.n_pixels,), -7, dtype=torch.int32, device=dev)
+        ff.set_trace(nview=sentinel)
+        tu, us0, us1 = ff.autotune(d, c, r, reps=5)
+        torch.cuda.synchronize()
+        assert (sentinel == -7).all()
+        ff.clear_trace()
+        assert 0 < us1 <= us0
+        assert ff.tuning() == tu.as_dict()
+        assert 1 <= tu.count_chunks <= 64 and tu.emit_blocks >= 1 and tu.prefetch_tiles >= 0
+        _same(base, run_gpu(ff, fr, torch, with_trace=False), with_trace=False)
+    finally:
+        ff.close()
+
+
+def test_autotune_rejects_bad_reps(ffmod):
+    rig, _, fr = S.config1()
+    ff = ffmod.FuseFlow(rig)
+    dev = torch.device("cuda")
+    try:
+        d = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.depth]
+        c = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.conf]
+        r = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in fr.rgb]
+        for reps in (2, 102):
+            with pytest.raises(ffmod.FuseFlowError):
+                ff.autotune(d, c, r, reps=reps)
+    finally:
+        ff.close()
+
+
+def test_server_autotune_needs_an_idle_rig_and_keeps_results(ffmod):
+    from paper_2602_01035_gb300 import serving as SV
+    rig, _, fr = S.config1()
+    ff = ffmod.FuseFlow(rig)
+    try:
+        alone = run_gpu(ff, fr, torch, with_trace=False)
+    finally:
+        ff.close()
+    srv = SV.Server(4 << 30)
+    try:
+        rid = srv.add_rig(rig, n_slots=2)
+        pf = SV.pinned_frame(fr)
+        hc = SV.HostCloud(srv.rigs[rid]["capacity"])
+        srv.submit(rid, pf, hc)
+        with pytest.raises(ffmod.FuseFlowError):          # a frame is in flight
+            srv.autotune(rid, pf, reps=3)
+        srv.drain()
+        tu, us0, us1 = srv.autotune(rid, pf, reps=3)
+        assert 0 < us1 <= us0
+        outs = [SV.HostCloud(srv.rigs[rid]["capacity"]) for _ in range(3)]
+        reqs = {srv.submit(rid, pf, h): h for h in outs}
+        for req, _, status, st in srv.drain():
+            assert status == ffmod.FUSEFLOW_OK
+            got = reqs[req].cells(st["n_cells"])
+            for k in ("pos", "rgb", "weight", "count", "rep", "key"):
+                assert np.array_equal(got[k], alone["cells"][k]), k
+    finally:
+        srv.close()
