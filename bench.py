@@ -468,6 +468,50 @@ def run_ours(args, rank, world, local_rank):
                             "algorithmic_bytes_per_launch": int(conf_bytes), "peak_source": peak_kind,
                             "note": "optional producer of Eq. 3, not part of the fused step"}
 
+    # ------------------------------------------------------------ depth screen D^r (Eq. 8)
+    # (an optional stage, off by default): the screen alone over the pool's depth maps, and
+    # whole frames fused with the edge and range screen set, CUDA events on the stream
+    ffs = F.FuseFlow(rig, screen_edge_rel=0.05, screen_min_m=0.3, screen_max_m=8.0)
+    scr_out = [torch.empty_like(t) for t in dtensors[0][0]]
+    scr_ptrs = [t.data_ptr() for t in scr_out]
+    for i in range(3):
+        F.fuseflow_screen_depth(ffs.ctx, dtensors[i % len(dtensors)][3], scr_ptrs, sh)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_scr = 200
+    s0.record(stream)
+    for i in range(n_scr):
+        F.fuseflow_screen_depth(ffs.ctx, dtensors[i % len(dtensors)][3], scr_ptrs, sh)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    scr_ms = s0.elapsed_time(s1) / n_scr
+    scr_bytes = 2 * depth_bytes * px
+    stages["screen"] = {"bound": "hbm", "achieved": round(scr_bytes / (scr_ms / 1e3) / 1e9, 1),
+                        "peak": peak, "unit": "GB/s",
+                        "frac": round(scr_bytes / (scr_ms / 1e3) / 1e9 / peak, 4),
+                        "traffic": traffic.get("screen"), "launch_ms": round(scr_ms, 5),
+                        "algorithmic_bytes_per_launch": int(scr_bytes), "peak_source": peak_kind,
+                        "note": "optional D^r of Eq. 8 (edge and range screen), off by default"}
+    if not args.no_autotune:
+        d0 = dtensors[0]
+        ffs.autotune(d0[0], d0[1], d0[2], reps=9, stream=sh)
+    for i in range(4):
+        t = dtensors[i % len(dtensors)]
+        F.fuseflow_fuse_frame(ffs.ctx, t[3], t[4], t[5], sh)
+    n_sf = min(FPS, 200)
+    s0.record(stream)
+    for i in range(n_sf):
+        t = dtensors[i % len(dtensors)]
+        F.fuseflow_fuse_frame(ffs.ctx, t[3], t[4], t[5], sh)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    sfs_ms = s0.elapsed_time(s1) / n_sf
+    sst, sstats = ffs.stats(sh, check=False)
+    screened = {"frames_per_s": round(1e3 / sfs_ms, 2), "vs_plain": round((ms / (args.steps * FPS)) / sfs_ms, 4),
+                "status_ok": sst == F.FUSEFLOW_OK, "n_valid": int(sstats.n_valid),
+                "n_valid_unscreened": int(st.n_valid), "cells_per_frame": int(sstats.n_cells),
+                "settings": "screen_edge_rel 0.05, screen_min_m 0.3, screen_max_m 8.0"}
+    ffs.close()
+
     # ------------------------------------------------------------ end to end (host buffers)
     # The public serving API on this rig: frames from pinned host memory, results into
     # pinned host arrays, `slots` frames in flight (copies overlap other frames' kernels).
@@ -553,7 +597,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "path_roofline": path_roof,
         "stage_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "stage_roofline": stages,
-        "graph_replay": graph_line, "batched": batched, "top3_variant": top3, "serving": serving, "other_configs": configs,
+        "graph_replay": graph_line, "batched": batched, "top3_variant": top3,
+        "screened_variant": screened, "serving": serving, "other_configs": configs,
         "e2e": e2e, "gpu_launches": int(args.steps * FPS * KERNELS_PER_FRAME),
         "cells_per_frame": int(n_cells), "status_ok": ok_status,
         "clocks": clocks, "cpu_baseline": cpu,

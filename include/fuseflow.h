@@ -73,6 +73,19 @@ typedef struct {
                                (ties to the lowest pixel index), with consistency computed
                                for those alone; 0 = every member (default); at most 7 */
     int64_t max_cells;      /* output capacity in cells; 0 = max(65536, pixels / 8) */
+    /* Depth preprocessing D^r of Eq. 8 ("filtered or screened"; the paper gives no rule, so
+     * this one is stated here).  A screened-out pixel counts as invalid everywhere: in the
+     * back-projection and in the other views' consistency gathers of Eq. 5.  All three are
+     * off by default (<= 0), and then D^r = D.  Decisions are taken in float32 on depth
+     * units: bounds b_u = (float)(b_m / depth_scale); a valid depth d is kept iff
+     * d >= min_u (when set) and d <= max_u (when set); then, with the edge screen on, d is
+     * screened out iff one of its 4-neighbours inside the image, itself valid and within
+     * the bounds, has fabsf(d - d') > (float)screen_edge_rel * d (flying pixels at depth
+     * discontinuities).  Neighbours are judged on the range-screened image, once. */
+    double screen_min_m;
+    double screen_max_m;
+    float screen_edge_rel;
+    int32_t reserved1;      /* 0 */
 } fuseflow_params;
 
 /* Frame statistics; written on the device by fuseflow_fuse_frame. */
@@ -188,6 +201,15 @@ typedef struct {
     double alpha, beta, gamma, delta;
 } fuseflow_conf_params;
 
+/* The screened depth D^r of Eq. 8 under the context's screen parameters (fuseflow_params),
+ * for callers that want it outside a fuse call (e.g. to feed fuseflow_confidence): for every
+ * camera i, reads depth_in[i] and writes depth_out[i] (DEVICE, the context's depth format,
+ * [H_i][W_i]; the two must not overlap), screened-out and invalid samples as 0.  Every
+ * fuse call of a context with a screen set applies the same step itself, into a scratch
+ * buffer of the context.  Asynchronous on `stream`.  Returns INVALID_ARG, CUDA. */
+int fuseflow_screen_depth(fuseflow_ctx *ctx, const void *const *depth_in, void *const *depth_out,
+                          void *stream);
+
 /* Eq. 3's printed constants: alpha = beta = 0.5, gamma = delta = 1. */
 void fuseflow_default_conf_params(fuseflow_conf_params *cp);
 
@@ -228,7 +250,7 @@ const char *fuseflow_stage_name(int stage);
  *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
  *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
  *                   depth rows into L2; 0 turns the prefetch off
- * fuseflow_create picks count_chunks for one wave of three count blocks per SM,
+ * fuseflow_create picks count_chunks for one wave of three count blocks per SM (at most 8),
  * emit_blocks = 8 blocks per SM and prefetch_tiles = one wave of assign blocks. */
 typedef struct fuseflow_tuning {
   int32_t count_chunks;

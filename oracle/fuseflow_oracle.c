@@ -22,6 +22,9 @@
  *    edge s0 / 2^l.  Points whose finest-level index leaves [-2^19, 2^19) are dropped.
  *  - Sec. II.5(2)a keeps every gated member of a cell in the fusion; the representative
  *    is the member of largest C, ties to the lowest pixel index.
+ *  - Eq. 8's D^r ("filtered or screened") has no stated rule; orc_screen_depth gives the
+ *    one read here (a depth range and a relative-jump screen against 4-neighbours), off
+ *    by default so that D^r = D.
  *  - Eq. 11 is read as the normalised weighted mean over the cell's members (positions
  *    and colours).  The mean is evaluated with weights divided by the cell's largest
  *    weight, which leaves it unchanged and keeps it defined when every weight underflows.
@@ -84,6 +87,52 @@ static int depth_at(const void *buf, int fmt, int64_t idx, double scale, double 
     if (!(raw > 0.0) || !isfinite(raw)) return 0;
     *z = raw * scale;
     return 1;
+}
+
+/* ---------------------------------------------------------------- depth screen (D^r) */
+static float raw_as_float(const void *buf, int fmt, int64_t idx) {
+    if (fmt == ORC_DEPTH_U16) return (float)((const uint16_t *)buf)[idx];
+    if (fmt == ORC_DEPTH_F32) return ((const float *)buf)[idx];
+    return (float)((const double *)buf)[idx];
+}
+
+/* valid and within the screen's bounds (float32 comparisons on depth units) */
+static int screen_in_bounds(float d, float min_u, float max_u) {
+    if (!(d > 0.0f) || !isfinite(d)) return 0;
+    if (min_u > 0.0f && !(d >= min_u)) return 0;
+    if (max_u > 0.0f && !(d <= max_u)) return 0;
+    return 1;
+}
+
+int orc_screen_depth(const orc_params *p, int32_t w, int32_t h, const void *in, void *out) {
+    if (!p || !in || !out || w < 1 || h < 1 || p->depth_scale <= 0) return ORC_ERR_ARG;
+    const float min_u = p->screen_min_m > 0 ? (float)(p->screen_min_m / p->depth_scale) : 0.0f;
+    const float max_u = p->screen_max_m > 0 ? (float)(p->screen_max_m / p->depth_scale) : 0.0f;
+    const float rel = p->screen_edge_rel > 0.0f ? p->screen_edge_rel : 0.0f;
+    const int dx[4] = {-1, 1, 0, 0}, dy[4] = {0, 0, -1, 1};
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            const int64_t i = (int64_t)y * w + x;
+            const float d = raw_as_float(in, p->depth_format, i);
+            int keep = screen_in_bounds(d, min_u, max_u);
+            if (keep && rel > 0.0f) {
+                const float thr = rel * d;
+                for (int k = 0; k < 4 && keep; ++k) {
+                    const int xn = x + dx[k], yn = y + dy[k];
+                    if (xn < 0 || xn >= w || yn < 0 || yn >= h) continue;
+                    const float dn = raw_as_float(in, p->depth_format, (int64_t)yn * w + xn);
+                    if (screen_in_bounds(dn, min_u, max_u) && fabsf(d - dn) > thr) keep = 0;
+                }
+            }
+            if (p->depth_format == ORC_DEPTH_U16)
+                ((uint16_t *)out)[i] = keep ? ((const uint16_t *)in)[i] : 0;
+            else if (p->depth_format == ORC_DEPTH_F32)
+                ((float *)out)[i] = keep ? ((const float *)in)[i] : 0.0f;
+            else
+                ((double *)out)[i] = keep ? ((const double *)in)[i] : 0.0;
+        }
+    }
+    return ORC_OK;
 }
 
 /* ---------------------------------------------------------------- neighbour table */
@@ -199,10 +248,37 @@ static int cmp_rep(const void *pa, const void *pb) {
 }
 
 /* ---------------------------------------------------------------- the frame */
+static int fuse_frame_on(const orc_camera *cams, int32_t n, const orc_params *p,
+                         const void *const *depth, const float *const *conf,
+                         const uint8_t *const *rgb, orc_points *pts, orc_cells *cells,
+                         int64_t cell_capacity, orc_stats *st);
+
+/* Eq. 8's D^r first (when a screen is set), then the frame on it */
 int orc_fuse_frame(const orc_camera *cams, int32_t n, const orc_params *p,
                    const void *const *depth, const float *const *conf,
                    const uint8_t *const *rgb, orc_points *pts, orc_cells *cells,
                    int64_t cell_capacity, orc_stats *st) {
+    if (!cams || n < 1 || !p || !depth) return ORC_ERR_ARG;
+    if (!(p->screen_min_m > 0) && !(p->screen_max_m > 0) && !(p->screen_edge_rel > 0.0f))
+        return fuse_frame_on(cams, n, p, depth, conf, rgb, pts, cells, cell_capacity, st);
+    const size_t esz = p->depth_format == ORC_DEPTH_U16 ? 2 : p->depth_format == ORC_DEPTH_F32 ? 4 : 8;
+    void **dr = (void **)calloc((size_t)n, sizeof(void *));
+    int rc = dr ? ORC_OK : ORC_ERR_NOMEM;
+    for (int i = 0; i < n && rc == ORC_OK; ++i) {
+        dr[i] = malloc(esz * (size_t)cams[i].width * (size_t)cams[i].height);
+        rc = dr[i] ? orc_screen_depth(p, cams[i].width, cams[i].height, depth[i], dr[i]) : ORC_ERR_NOMEM;
+    }
+    if (rc == ORC_OK)
+        rc = fuse_frame_on(cams, n, p, (const void *const *)dr, conf, rgb, pts, cells, cell_capacity, st);
+    for (int i = 0; dr && i < n; ++i) free(dr[i]);
+    free(dr);
+    return rc;
+}
+
+static int fuse_frame_on(const orc_camera *cams, int32_t n, const orc_params *p,
+                         const void *const *depth, const float *const *conf,
+                         const uint8_t *const *rgb, orc_points *pts, orc_cells *cells,
+                         int64_t cell_capacity, orc_stats *st) {
     if (!cams || n < 1 || !p || !depth || !conf || !rgb || !st) return ORC_ERR_ARG;
     if (p->k_views < 1 || p->sigma_m <= 0 || p->coarse_cell_m <= 0 || p->max_level < 0 ||
         p->max_level > 14 || p->n_min < 1 || p->depth_scale <= 0 || p->top_k < 0)

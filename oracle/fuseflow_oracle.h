@@ -47,6 +47,9 @@ typedef struct {
     double band_az;        /* report projections with |a_z| below band_az metres */
     int32_t top_k;         /* Sec. II.5(2)a: fuse only the top_k members of a cell by C
                               (ties to the lowest pixel index); 0 = every member */
+    double screen_min_m;   /* D^r of Eq. 8 (see orc_screen_depth); <= 0: no lower bound */
+    double screen_max_m;   /* <= 0: no upper bound */
+    float screen_edge_rel; /* <= 0: no edge screen */
 } orc_params;
 
 /* Per-pixel outputs, arrays of n_pixels entries in global pixel order
@@ -89,6 +92,17 @@ void orc_default_params(orc_params *p);
 
 /* Static neighbour table: for each camera the K-1 other cameras used in Eq. 7. */
 int orc_neighbours(const orc_camera *cams, int32_t n_cams, int32_t k_views, int32_t *out);
+
+/* D^r of Eq. 8, "depth after necessary preprocessing (e.g. filtered or screened)".  The
+ * paper states no rule; the one read here: in depth units, with every comparison in
+ * float32 (the same decision the GPU takes), bounds b_u = (float)(b_m / depth_scale);
+ * a valid sample d (> 0, finite) is kept iff d >= min_u (bound set) and d <= max_u (bound
+ * set); a kept sample is then screened out iff one of its 4-neighbours inside the image
+ * is valid, within the bounds, and fabsf(d - d') > (float)screen_edge_rel * d.  Screened
+ * and invalid samples are written as 0 in the input's format.  orc_fuse_frame applies it
+ * to every camera first when any of the three settings is > 0, and uses D^r for both the
+ * back-projection and the consistency gathers. */
+int orc_screen_depth(const orc_params *p, int32_t w, int32_t h, const void *in, void *out);
 
 int orc_fuse_frame(const orc_camera *cams, int32_t n_cams, const orc_params *p,
                    const void *const *depth, const float *const *conf,

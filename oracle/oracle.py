@@ -35,7 +35,9 @@ class _Params(C.Structure):
                 ("coarse_cell_m", C.c_double), ("max_level", C.c_int32), ("n_min", C.c_int32),
                 ("depth_format", C.c_int32), ("use_conf", C.c_int32), ("depth_scale", C.c_double),
                 ("use_consistency", C.c_int32), ("row_step", C.c_int32), ("band_m", C.c_double),
-                ("band_px", C.c_double), ("band_az", C.c_double), ("top_k", C.c_int32)]
+                ("band_px", C.c_double), ("band_az", C.c_double), ("top_k", C.c_int32),
+                ("screen_min_m", C.c_double), ("screen_max_m", C.c_double),
+                ("screen_edge_rel", C.c_float)]
 
 
 _P = C.c_void_p
@@ -91,6 +93,9 @@ def _load():
         lib.orc_confidence.restype = C.c_int
         lib.orc_confidence.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(_Params),
                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p]
+        lib.orc_screen_depth.restype = C.c_int
+        lib.orc_screen_depth.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, C.c_void_p,
+                                         C.c_void_p]
         lib.orc_default_params.restype = None
         lib.orc_default_params.argtypes = [C.POINTER(_Params)]
         _lib = lib
@@ -236,6 +241,26 @@ def confidence(depth, depth_format: str, depth_scale: float, alpha=0.5, beta=0.5
                             out.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"orc_confidence failed with status {rc}")
+    return out
+
+
+def screen_depth(depth, depth_format: str, depth_scale: float, screen_min_m: float = 0.0,
+                 screen_max_m: float = 0.0, screen_edge_rel: float = 0.0) -> np.ndarray:
+    """D^r of Eq. 8 of one depth image under the stated screen rule (oracle)."""
+    lib = _load()
+    prm = _Params()
+    lib.orc_default_params(C.byref(prm))
+    prm.depth_format = DEPTH_FORMATS[depth_format]
+    prm.depth_scale = depth_scale
+    prm.screen_min_m, prm.screen_max_m = screen_min_m, screen_max_m
+    prm.screen_edge_rel = screen_edge_rel
+    want = {"u16": np.uint16, "f32": np.float32, "f64": np.float64}[depth_format]
+    d = np.ascontiguousarray(depth, dtype=want)
+    h, w = d.shape
+    out = np.empty_like(d)
+    rc = lib.orc_screen_depth(C.byref(prm), w, h, d.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"orc_screen_depth failed with status {rc}")
     return out
 
 

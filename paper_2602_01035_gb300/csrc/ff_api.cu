@@ -46,6 +46,9 @@ struct fuseflow_ctx {
   size_t stage_bytes = 0;
   // per-block sums of the MC error (Eq. 12)
   void* d_mc = nullptr;
+  // D^r of Eq. 8 when a depth screen is set (per camera, 256-byte aligned)
+  void* d_screen = nullptr;
+  size_t screen_bytes = 0;
   // stage timing ring
   bool timing = false;
   std::vector<cudaEvent_t> events;     // kTimingRing * (FUSEFLOW_N_STAGES + 1)
@@ -152,7 +155,27 @@ int validate(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* extr, i
   if (!(p->depth_scale > 0) || !finite(p->depth_scale)) return FUSEFLOW_ERR_INVALID_ARG;
   if (p->max_cells < 0 || p->max_cells > (1ll << 30)) return FUSEFLOW_ERR_INVALID_ARG;
   if (p->top_k < 0 || p->top_k > kMaxTopK) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!finite(p->screen_min_m) || !finite(p->screen_max_m) || !std::isfinite(p->screen_edge_rel) ||
+      p->reserved1 != 0)
+    return FUSEFLOW_ERR_INVALID_ARG;
+  if (p->screen_min_m > 0 && p->screen_max_m > 0 && p->screen_min_m > p->screen_max_m)
+    return FUSEFLOW_ERR_INVALID_ARG;
   return FUSEFLOW_OK;
+}
+
+bool screen_set(const fuseflow_params* p) {
+  return p->screen_min_m > 0 || p->screen_max_m > 0 || p->screen_edge_rel > 0.0f;
+}
+
+// Screen bounds in depth units and image sizes (the buffers are filled in by the caller).
+ScreenArgs screen_args(const fuseflow_intrinsics* intr, int n_cams, const fuseflow_params* p) {
+  ScreenArgs a{};
+  a.n_cams = n_cams;
+  for (int i = 0; i < n_cams; ++i) { a.W[i] = intr[i].width; a.H[i] = intr[i].height; }
+  a.min_u = p->screen_min_m > 0 ? (float)(p->screen_min_m / p->depth_scale) : 0.0f;
+  a.max_u = p->screen_max_m > 0 ? (float)(p->screen_max_m / p->depth_scale) : 0.0f;
+  a.edge_rel = p->screen_edge_rel > 0.0f ? p->screen_edge_rel : 0.0f;
+  return a;
 }
 
 // Rig constants shared by fuseflow_create and the static entry point: per-camera
@@ -288,6 +311,7 @@ void fuseflow_destroy(fuseflow_ctx* ctx) {
   cudaFree(ctx->d_tables);
   cudaFree(ctx->d_out);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_screen);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   cudaSetDevice(prev);
   delete ctx;
@@ -335,14 +359,19 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   ctx->geo.n_cams = n_cams;
   ctx->geo.top_k = params->top_k;
   ctx->geo.depth_f32 = rig->depth_f32;
+  ctx->geo.max_px = max_px;
+  ctx->geo.scr = screen_args(intr, n_cams, params);
+  ctx->geo.screen = screen_set(params) ? 1 : 0;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   {
-    // several 2048-pixel chunks per count block: one wave of 3 blocks per SM
+    // several 2048-pixel chunks per count block: one wave of 3 blocks per SM, but at most 8
+    // chunks, since a block's table of coarse cells (2048 entries) spills to the global
+    // table when one block covers too much of the scene
     long long total_chunks = 0;
     for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 2047) / 2048;
     const long long per = (total_chunks + 3ll * sms - 1) / (3ll * sms);
-    ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
+    ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(8, per));
     ctx->max_chunks = (max_px + 2047) / 2048;
     ctx->geo.count_blocks_x = (int)((ctx->max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
@@ -387,13 +416,27 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   fill_block_consts(*rig, bconst.data());
   const size_t pray_at = align_up(sizeof(BlockConst) * (size_t)n_cams, 256);
   const size_t blocks_bytes = pray_at + sizeof(float4) * pray.size();
-  if (cudaMalloc(&ctx->d_rig, sizeof(RigDev)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_rays, sizeof(float2) * rays.size()) != cudaSuccess ||
-      cudaMalloc(&ctx->d_blocks, blocks_bytes) != cudaSuccess ||
-      cudaMalloc(&ctx->d_tables, ctx->table_bytes) != cudaSuccess ||
-      cudaMalloc(&ctx->d_out, ctx->out_bytes) != cudaSuccess) {
-    status = FUSEFLOW_ERR_OUT_OF_MEMORY;
+  if (ctx->geo.screen) {
+    const size_t dsz = rig->depth_f32 ? 4 : 2;
+    std::vector<size_t> at((size_t)n_cams);
+    for (int i = 0; i < n_cams; ++i) {
+      at[i] = ctx->screen_bytes;
+      ctx->screen_bytes += align_up((size_t)intr[i].width * intr[i].height * dsz, 256);
+    }
+    if (cudaMalloc(&ctx->d_screen, ctx->screen_bytes) != cudaSuccess) {
+      ctx->d_screen = nullptr;
+      status = FUSEFLOW_ERR_OUT_OF_MEMORY;
+    } else {
+      for (int i = 0; i < n_cams; ++i) ctx->geo.scr.out[i] = static_cast<char*>(ctx->d_screen) + at[i];
+    }
   }
+  if (status == FUSEFLOW_OK &&
+      (cudaMalloc(&ctx->d_rig, sizeof(RigDev)) != cudaSuccess ||
+       cudaMalloc(&ctx->d_rays, sizeof(float2) * rays.size()) != cudaSuccess ||
+       cudaMalloc(&ctx->d_blocks, blocks_bytes) != cudaSuccess ||
+       cudaMalloc(&ctx->d_tables, ctx->table_bytes) != cudaSuccess ||
+       cudaMalloc(&ctx->d_out, ctx->out_bytes) != cudaSuccess))
+    status = FUSEFLOW_ERR_OUT_OF_MEMORY;
   if (status == FUSEFLOW_OK) {
     char* b = static_cast<char*>(ctx->d_tables);
     Tables& t = ctx->tab;
@@ -609,6 +652,21 @@ int fuseflow_fuse_frame_host(fuseflow_ctx* ctx, const void* const* depth, const 
   return st;
 }
 
+int fuseflow_screen_depth(fuseflow_ctx* ctx, const void* const* depth_in, void* const* depth_out,
+                          void* stream) {
+  if (!ctx || !depth_in || !depth_out) return FUSEFLOW_ERR_INVALID_ARG;
+  ScreenArgs a = ctx->geo.scr;
+  for (int i = 0; i < ctx->n_cams; ++i) {
+    if (!depth_in[i] || !depth_out[i] || depth_in[i] == depth_out[i]) return FUSEFLOW_ERR_INVALID_ARG;
+    a.in[i] = depth_in[i];
+    a.out[i] = depth_out[i];
+  }
+  return launch_screen(a, ctx->geo.depth_f32 != 0, ctx->geo.max_px, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? FUSEFLOW_OK
+             : FUSEFLOW_ERR_CUDA;
+}
+
 void fuseflow_default_conf_params(fuseflow_conf_params* cp) {
   if (!cp) return;
   cp->alpha = 0.5;
@@ -819,10 +877,14 @@ struct Autotuner {
     long long total_chunks = 0;
     for (int i = 0; i < ctx->n_cams; ++i)
       total_chunks += ((long long)ctx->intr[i].width * ctx->intr[i].height + 2047) / 2048;
+    std::vector<int> chunks = {2, 4, 8, 16};
     for (int b : {1, 2, 3, 4, 6, 8}) {
-      fuseflow_tuning c = best;
       const long long per = (total_chunks + (long long)b * sms - 1) / ((long long)b * sms);
-      c.count_chunks = (int)std::max<long long>(1, std::min<long long>(64, per));
+      chunks.push_back((int)std::max<long long>(1, std::min<long long>(64, per)));
+    }
+    for (int k : chunks) {
+      fuseflow_tuning c = best;
+      c.count_chunks = k;
       if ((st = consider(c)) != FUSEFLOW_OK) return st;
     }
     for (int b : {1, 2, 4, 8, 16}) {
@@ -888,7 +950,9 @@ const char* fuseflow_stage_name(int stage) {
 int64_t fuseflow_num_pixels(const fuseflow_ctx* ctx) { return ctx ? ctx->n_px : 0; }
 int64_t fuseflow_capacity(const fuseflow_ctx* ctx) { return ctx ? ctx->max_cells : 0; }
 int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
-  return ctx ? (int64_t)(ctx->table_bytes + ctx->out_bytes + ctx->stage_bytes + sizeof(RigDev)) : 0;
+  return ctx ? (int64_t)(ctx->table_bytes + ctx->out_bytes + ctx->stage_bytes + ctx->screen_bytes +
+                         sizeof(RigDev))
+             : 0;
 }
 
 }  // extern "C"
@@ -1033,6 +1097,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   if (v != FUSEFLOW_OK) return v;
   if (!depth || !conf || !rgb || !pos || !rgb_out || !weight || !count || !rep || !key || !stats)
     return FUSEFLOW_ERR_INVALID_ARG;
+  if (screen_set(params)) return FUSEFLOW_ERR_INVALID_ARG;     // no D^r buffer in the arena
   long long n_px = 0, max_px = 0, n_rays = 0;
   for (int i = 0; i < n_cams; ++i) {
     const long long px = (long long)intr[i].width * intr[i].height;

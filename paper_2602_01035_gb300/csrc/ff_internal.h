@@ -66,9 +66,24 @@ struct OutDev {
 // Assign-step prefetch distance (tiles) that turns the L2 prefetch off.
 constexpr int kNoPrefetch = 1 << 30;
 
+// Depth preprocessing D^r of Eq. 8: range screen in depth units, then the edge screen
+// against valid in-range 4-neighbours (bounds and ratio <= 0 are off).
+struct ScreenArgs {
+  const void* in[kMaxCams];
+  void* out[kMaxCams];
+  int W[kMaxCams], H[kMaxCams];
+  int n_cams;
+  float min_u, max_u;
+  float edge_rel;
+};
+cudaError_t launch_screen(const ScreenArgs& a, bool depth_f32, long long max_px, cudaStream_t s);
+
 struct Geometry {
   int n_cams;
   int depth_f32;
+  int screen;                    // a screen is set: fuse calls write D^r into screen_buf first
+  ScreenArgs scr;                // bounds, sizes and the context's D^r buffers (out)
+  long long max_px;
   int count_blocks_x;            // blocks per camera of the coarse-count step (max over cams)
   int count_chunks;              // 2048-pixel chunks per block of the coarse-count step
   int emit_blocks;

@@ -1577,6 +1577,41 @@ __global__ void k_init_tables(Tables t, unsigned fcap, unsigned ccap) {
   }
 }
 
+// ------------------------------------------------------------------ depth screen
+// D^r of Eq. 8 (stated rule: include/fuseflow.h, fuseflow_params): a valid sample within
+// the depth-unit bounds is kept unless a valid in-bounds 4-neighbour differs from it by more
+// than edge_rel times its value; every decision in float32, screened samples become 0.
+template <typename DT>
+__device__ __forceinline__ bool screen_keep(DT d, float min_u, float max_u) {
+  if (!Depth<DT>::valid(d)) return false;
+  const float z = Depth<DT>::z(d);
+  return (min_u <= 0.0f || z >= min_u) && (max_u <= 0.0f || z <= max_u);
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_screen(ScreenArgs a) {
+  const int cam = blockIdx.y;
+  const unsigned W = (unsigned)a.W[cam], H = (unsigned)a.H[cam], n = W * H;   // W H <= 2^30
+  const DT* __restrict__ in = static_cast<const DT*>(a.in[cam]);
+  DT* __restrict__ out = static_cast<DT*>(a.out[cam]);
+  for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const DT d = __ldg(in + p);
+    bool keep = screen_keep<DT>(d, a.min_u, a.max_u);
+    if (keep && a.edge_rel > 0.0f) {
+      const unsigned y = p / W, x = p - y * W;
+      const float z = Depth<DT>::z(d), thr = __fmul_rn(a.edge_rel, z);
+      auto jump = [&](unsigned q) {
+        const DT e = __ldg(in + q);
+        return screen_keep<DT>(e, a.min_u, a.max_u) && fabsf(__fsub_rn(z, Depth<DT>::z(e))) > thr;
+      };
+      if ((x > 0 && jump(p - 1)) || (x + 1 < W && jump(p + 1)) || (y > 0 && jump(p - W)) ||
+          (y + 1 < H && jump(p + W)))
+        keep = false;
+    }
+    out[p] = keep ? d : (DT)0;
+  }
+}
+
 // Dynamic shared memory limit of the assign kernels for one depth type, set once (the
 // first call comes from context creation, outside any stream capture).
 template <typename DT>
@@ -1596,7 +1631,7 @@ cudaError_t set_assign_attributes() {
 }
 
 template <typename DT>
-cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
+cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp_in, const Tables& t,
                          const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
                          cudaEvent_t* ev) {
   const cudaError_t ae = set_assign_attributes<DT>();
@@ -1605,6 +1640,15 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   mark(0);
   cudaError_t err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
   if (err != cudaSuccess) return err;
+  FramePtrs fp = fp_in;
+  if (geo.screen) {                        // D^r of Eq. 8 into the context's buffers
+    ScreenArgs a = geo.scr;
+    for (int i = 0; i < geo.n_cams; ++i) {
+      a.in[i] = fp_in.depth[i];
+      fp.depth[i] = a.out[i];
+    }
+    if ((err = launch_screen(a, sizeof(DT) == 4, geo.max_px, s)) != cudaSuccess) return err;
+  }
   mark(1);
   k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x,
                                                                        geo.count_chunks);
@@ -1704,6 +1748,14 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
   const float occl = (float)(occlusion_m / unit_m);      // +inf stays +inf
   if (depth_f32) k_mc<float><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
   else k_mc<uint16_t><<<g, kThreads, 0, s>>>(rig, fp, pos, n, inv, um, occl, err, nvis, bsum, bcnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen(const ScreenArgs& a, bool depth_f32, long long max_px, cudaStream_t s) {
+  const unsigned bx = (unsigned)std::min<long long>((max_px + kThreads - 1) / kThreads, 4096);
+  const dim3 grid(std::max(1u, bx), a.n_cams);
+  if (depth_f32) k_screen<float><<<grid, kThreads, 0, s>>>(a);
+  else k_screen<uint16_t><<<grid, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

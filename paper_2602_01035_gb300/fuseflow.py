@@ -41,7 +41,9 @@ class fuseflow_params(C.Structure):
     _fields_ = [("tau", C.c_float), ("k_views", C.c_int32), ("sigma_m", C.c_double),
                 ("coarse_cell_m", C.c_double), ("max_level", C.c_int32), ("n_min", C.c_int32),
                 ("depth_format", C.c_int32), ("use_conf", C.c_int32), ("depth_scale", C.c_double),
-                ("use_consistency", C.c_int32), ("top_k", C.c_int32), ("max_cells", C.c_int64)]
+                ("use_consistency", C.c_int32), ("top_k", C.c_int32), ("max_cells", C.c_int64),
+                ("screen_min_m", C.c_double), ("screen_max_m", C.c_double),
+                ("screen_edge_rel", C.c_float), ("reserved1", C.c_int32)]
 
 
 class fuseflow_stats(C.Structure):
@@ -122,6 +124,8 @@ EXPORTS = {
                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fuseflow_screen_depth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.c_void_p]),
     "fuseflow_default_conf_params": (None, [C.POINTER(fuseflow_conf_params)]),
     "fuseflow_confidence": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                       C.POINTER(fuseflow_conf_params), C.c_void_p]),
@@ -341,6 +345,12 @@ def fuseflow_confidence(ctx, depth_ptrs, out_ptrs, stream: int = 0, **weights) -
         setattr(cp, k, v)
     _check(load().fuseflow_confidence(ctx, _ptr_array(depth_ptrs), _ptr_array(out_ptrs),
                                       C.byref(cp), C.c_void_p(stream)), "fuseflow_confidence")
+
+
+def fuseflow_screen_depth(ctx, in_ptrs, out_ptrs, stream: int = 0) -> None:
+    """D^r of Eq. 8 (the context's screen parameters) of every camera into device buffers."""
+    _check(load().fuseflow_screen_depth(ctx, _ptr_array(in_ptrs), _ptr_array(out_ptrs),
+                                        C.c_void_p(stream)), "fuseflow_screen_depth")
 
 
 MC_OCCLUSION_M = 0.05   # default occlusion margin of Eq. 12's visibility test, metres

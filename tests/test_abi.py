@@ -61,7 +61,10 @@ def _rig(n=2):
                                          ("coarse_cell_m", 0.0), ("max_level", 15),
                                          ("max_level", -1), ("n_min", 0), ("depth_format", 7),
                                          ("depth_scale", 0.0), ("max_cells", -5),
-                                         ("tau", float("nan")), ("tau", -0.5)])
+                                         ("tau", float("nan")), ("tau", -0.5),
+                                         ("screen_min_m", float("inf")),
+                                         ("screen_max_m", float("nan")),
+                                         ("screen_edge_rel", float("inf")), ("reserved1", 3)])
 def test_create_rejects_bad_parameters(ffmod, field, value):
     rig = _rig()
     intr, extr = ffmod.rig_arrays(rig)
@@ -149,3 +152,50 @@ def test_graph_entry_points_reject_bad_arguments_without_a_gpu(ffmod):
     assert lib.fuseflow_graph_create(None, None, None, None, C.byref(g)) == bad
     assert lib.fuseflow_graph_launch(None, None, None) == bad
     lib.fuseflow_graph_destroy(None)
+
+
+def test_screen_bounds_must_be_ordered_and_static_entry_has_no_screen(ffmod):
+    lib = ffmod.load()
+    rig = _rig()
+    intr, extr = ffmod.rig_arrays(rig)
+    p = ffmod.fuseflow_default_params()
+    assert p.screen_min_m == 0 and p.screen_max_m == 0 and p.screen_edge_rel == 0
+    p.screen_min_m, p.screen_max_m = 3.0, 2.0
+    ctx = C.c_void_p()
+    assert lib.fuseflow_create(intr, extr, 2, C.byref(p), C.byref(ctx)) == 1 and not ctx.value
+    # the allocation-free entry has no buffer for D^r: refused before any GPU work
+    p = ffmod.fuseflow_default_params(screen_edge_rel=0.05)
+    dummy = (C.c_void_p * 2)(1, 1)
+    out = C.c_void_p(1)
+    st = lib.fuseflow_fuse_frame_static(intr, extr, 2, C.byref(p), dummy, dummy, dummy, out, out,
+                                        out, out, out, out, out, None)
+    assert st == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_screen_depth(None, dummy, dummy, None) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_the_header(ffmod, tmp_path):
+    """sizeof/offsetof of every ABI struct from a C compiler against the ctypes binding."""
+    import subprocess
+    structs = {"fuseflow_params": ffmod.fuseflow_params, "fuseflow_stats": ffmod.fuseflow_stats,
+               "fuseflow_cloud": ffmod.fuseflow_cloud, "fuseflow_trace": ffmod.fuseflow_trace,
+               "fuseflow_intrinsics": ffmod.fuseflow_intrinsics,
+               "fuseflow_extrinsics": ffmod.fuseflow_extrinsics,
+               "fuseflow_conf_params": ffmod.fuseflow_conf_params,
+               "fuseflow_tuning": ffmod.fuseflow_tuning,
+               "fuseflow_host_cloud": ffmod.fuseflow_host_cloud,
+               "fuseflow_completion": ffmod.fuseflow_completion}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fuseflow.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"
