@@ -63,7 +63,7 @@ def test_frames_with_a_screen_match_the_oracle(ffmod, oracle_mod, case, screen, 
     params = dict(screen, top_k=top_k)
     ff = ffmod.FuseFlow(rig, **params)
     try:
-        gpu = run_gpu(ff, fr, torch, with_trace=case != 3)
+        gpu = run_gpu(ff, fr, torch, with_trace=True)     # the trace places boundary points
         assert gpu["status"] == ffmod.FUSEFLOW_OK, gpu["stats"]
     finally:
         ff.close()

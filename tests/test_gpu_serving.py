@@ -129,3 +129,33 @@ def test_capacity_of_the_host_arrays_is_reported(mods):
         assert status == F.FUSEFLOW_ERR_CAPACITY and st["n_cells"] > 10
     finally:
         srv.close()
+
+
+def test_top_k_and_screened_rigs_serve_the_same_results(mods):
+    F, SV = mods
+    r1, _, f1 = S.config1()
+    r2 = S.tiny_rig(n=3, width=96, height=64, spread_deg=25.0, fx=80.0, fy=78.0)
+    f2 = S.random_frame(r2, seed=23, zero_frac=0.02, flying_frac=0.02)
+    cases = [(r1, f1, {"top_k": 3}), (r2, f2, {"screen_edge_rel": 0.03, "screen_max_m": 4.0})]
+    alone = []
+    for rig, fr, prm in cases:
+        ff = F.FuseFlow(rig, **prm)
+        try:
+            alone.append(run_gpu(ff, fr, torch, with_trace=False))
+        finally:
+            ff.close()
+    srv = SV.Server(4 << 30)
+    try:
+        rids = [srv.add_rig(rig, n_slots=2, **prm) for rig, _, prm in cases]
+        frames = [SV.pinned_frame(fr) for _, fr, _ in cases]
+        bufs = {}
+        for k in (0, 1, 1, 0):
+            hc = SV.HostCloud(srv.rigs[rids[k]]["capacity"])
+            bufs[srv.submit(rids[k], frames[k], hc)] = (k, hc)
+        for req, _, status, st in srv.drain():
+            k, hc = bufs[req]
+            assert status == F.FUSEFLOW_OK
+            _same(hc.cells(st["n_cells"]), alone[k]["cells"])
+    finally:
+        srv.close()
+

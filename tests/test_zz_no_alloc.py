@@ -45,7 +45,8 @@ def _check_same(ref_cells, ref_stats, got, n):
     assert np.all(np.abs(c - ref_cells["rgb"]) <= 6e-3)
 
 
-def test_static_entry_point_matches_context_path_twice():
+@pytest.mark.parametrize("top_k", [0, 3])
+def test_static_entry_point_matches_context_path_twice(top_k):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2602_01035_gb300 import fuseflow as F
@@ -56,14 +57,14 @@ def test_static_entry_point_matches_context_path_twice():
     frames = [S.random_frame(rig, seed=s, flying_frac=0.01) for s in (31, 32)]
     cap = 8192
     for fr in frames:
-        ff = F.FuseFlow(rig, max_cells=cap)
+        ff = F.FuseFlow(rig, max_cells=cap, top_k=top_k)
         try:
             ref = run_gpu(ff, fr, torch, with_trace=False)
         finally:
             ff.close()
         assert ref["status"] == F.FUSEFLOW_OK and ref["stats"]["n_cells"] > 100
         p = F.fuseflow_default_params(depth_format=F.FUSEFLOW_DEPTH_U16,
-                                      depth_scale=rig.depth_scale, max_cells=cap)
+                                      depth_scale=rig.depth_scale, max_cells=cap, top_k=top_k)
         intr, extr = F.rig_arrays(rig)
         d = [torch.from_numpy(x).to(dev) for x in fr.depth]
         c = [torch.from_numpy(x).to(dev) for x in fr.conf]
