@@ -297,7 +297,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
  * change the process's memory footprint after start-up.  This call needs no context: it
  * takes the rig and parameters directly, calls no cudaMalloc, cudaFree or other
  * allocating routine (device or host), and keeps all of its scratch in one file-scope
- * device array of about 26 MiB that every GPU loading this library holds until exit.
+ * device array of about 23 MiB that every GPU loading this library holds until exit.
  *
  * Limits: at most 524,288 pixels per frame over all cameras, at most 65,536 ray-table
  * entries (sum over cameras of width + height), 2 (K - 1) times that at most 393,216

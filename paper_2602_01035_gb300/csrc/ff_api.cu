@@ -961,7 +961,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx* ctx) {
 // Allocation-free variant of fuseflow_fuse_frame.
 //
 // All scratch (rig constants, ray tables, hash tables, per-pixel records, scan buffers)
-// lives in one file-scope device array of kStaticBytes (about 21 MiB), held by every GPU
+// lives in one file-scope device array of kStaticBytes (about 23 MiB), held by every GPU
 // that loads this library until the process exits.  Host code never dereferences the
 // array's name: the device address comes from cudaGetSymbolAddress, taken once per device
 // on that device's first call (which also clears the hash tables and synchronizes the

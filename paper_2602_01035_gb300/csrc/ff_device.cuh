@@ -18,7 +18,7 @@ namespace ffl {
 
 constexpr int kMaxCams = 64;
 constexpr int kMaxK1 = 8;
-constexpr int kMaxTopK = 7;              // top-k keys travel in a partial record's 7 sums
+constexpr int kMaxTopK = 7;              // top-k keys travel in a partial record (rep + 6)
 constexpr unsigned long long kKeyEmpty = ~0ull;
 constexpr uint32_t kSlotNone = 0xffffffffu;
 constexpr int kFixShift = 36;            // per-cell fixed point: largest member weight ~ 2^36
@@ -95,15 +95,30 @@ struct TileIndex {
 // Per (tile, cell) partial result of the assign step, pushed onto its cell's list when it
 // is written.  Sums are exact integers in units of 2^-(kFixShift + mmin) of the tile's own
 // smallest weight exponent mmin; the reduce step shifts them to the cell's smallest one.
-struct __align__(16) Partial {
-  unsigned slot;                 // dense slot of the cell
-  unsigned count;                // members in the tile
-  int mmin;                      // smallest weight exponent m in the tile
+// Each sum is below 2^46 (at most 512 terms below 2^37), so 48 bits hold it: the record is
+// 64 bytes, two aligned 32-byte sectors.
+struct __align__(64) Partial {
+  unsigned long long rep;        // max of ordered(C) << 32 | ~g (top-k: the tile's first key)
   unsigned next;                 // next partial of the same cell, kSlotNone at the end
-  unsigned long long rep;        // max of ordered(C) << 32 | ~g
-  unsigned long long s[7];       // sums of w, w frac_x, w frac_y, w frac_z, w r, w g, w b
+  unsigned count;                // members in the tile
+  union {
+    struct {
+      int mmin;                  // smallest weight exponent m in the tile
+      unsigned lo[7];            // bits 0..31 of the sums of w, w frac_x, w frac_y, w frac_z,
+      unsigned short hi[7];      //   w r, w g, w b; bits 32..47
+      unsigned short pad;
+    } sum;
+    unsigned long long top[kMaxTopK - 1];   // top-k variant: the tile's keys 2..k
+  };
+  __device__ __forceinline__ void set_sum(int a, unsigned long long v) {
+    sum.lo[a] = (unsigned)v;
+    sum.hi[a] = (unsigned short)(v >> 32);
+  }
+  __device__ __forceinline__ unsigned long long get_sum(int a) const {
+    return ((unsigned long long)sum.hi[a] << 32) | sum.lo[a];
+  }
 };
-static_assert(sizeof(Partial) == 80, "partial record layout");
+static_assert(sizeof(Partial) == 64, "partial record layout");
 
 // Per dense cell slot: the cell's key, its list head and its smallest weight exponent, in
 // one 16-byte record so that the reduce step reads a single sector per cell.

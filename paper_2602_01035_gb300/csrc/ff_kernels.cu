@@ -568,11 +568,12 @@ constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 l
 
 // Writes partial p as record pi and pushes it onto its cell's list; true when it is the
 // cell's first partial of the frame (the caller then lists the cell).
-__device__ __forceinline__ bool file_partial(const Tables& t, Partial& p, unsigned long long key,
-                                             unsigned pi) {
-  SlotRec& rec = t.frec[p.slot];
+// mmin: the record's smallest weight exponent, INT_MAX for top-k records (no sums).
+__device__ __forceinline__ bool file_partial(const Tables& t, Partial& p, unsigned slot,
+                                             unsigned long long key, int mmin, unsigned pi) {
+  SlotRec& rec = t.frec[slot];
   rec.key = key;                                // the same value from every tile of the cell
-  atomicMin(&rec.mmin, p.mmin);
+  if (mmin != INT_MAX) atomicMin(&rec.mmin, mmin);
   p.next = atomicExch(&rec.head, pi);           // list push
   t.part[pi] = p;
   return p.next == kSlotNone;
@@ -925,19 +926,17 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
         }
       } else {                                  // a single-member partial of its own
         Partial p;
-        p.slot = s_fk[h];
+        const unsigned slot = s_fk[h];
         p.count = 1u;
-        p.mmin = 0;
         p.rep = key;
-        p.s[0] = key;
 #pragma unroll
-        for (int a = 1; a < 7; ++a) p.s[a] = 0ull;
+        for (int a = 0; a < kMaxTopK - 1; ++a) p.top[a] = 0ull;
         const unsigned pi = atomicAdd(&t.cnt->n_partials, 1u);
         if (pi >= t.max_partials) {
           atomicOr(&t.cnt->error, kErrPartials);
-        } else if (file_partial(t, p, fkey[j], pi)) {
+        } else if (file_partial(t, p, slot, fkey[j], INT_MAX, pi)) {
           const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
-          if (n < t.max_slots) t.fused[n] = p.slot;
+          if (n < t.max_slots) t.fused[n] = slot;
         }
       }
       continue;
@@ -963,22 +962,23 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       }
     } else {                                    // a single-member partial of its own
       Partial p;
-      p.slot = s_fk[hpos[j]];
+      const unsigned slot = s_fk[hpos[j]];
       p.count = 1u;
-      p.mmin = mexp[j];
+      p.sum.mmin = mexp[j];
+      p.sum.pad = 0;
       p.rep = ((unsigned long long)cord[j] << 32) | (unsigned)(~(unsigned)gi[j]);
 #pragma unroll
       for (int a = 0; a < 7; ++a) {
         unsigned lo, hi;
         split_round(v[a], lo, hi);
-        p.s[a] = ((unsigned long long)hi << kLoBits) + lo;
+        p.set_sum(a, ((unsigned long long)hi << kLoBits) + lo);
       }
       const unsigned pi = atomicAdd(&t.cnt->n_partials, 1u);
       if (pi >= t.max_partials) {
         atomicOr(&t.cnt->error, kErrPartials);
-      } else if (file_partial(t, p, fkey[j], pi)) {
+      } else if (file_partial(t, p, slot, fkey[j], mexp[j], pi)) {
         const unsigned n = atomicAdd(&t.cnt->n_cells, 1u);
-        if (n < t.max_slots) t.fused[n] = p.slot;
+        if (n < t.max_slots) t.fused[n] = slot;
       }
     }
   }
@@ -996,23 +996,23 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
       } else {
         const unsigned h = s_ep[e];
         Partial p;
-        p.slot = slot = s_fk[h];
+        slot = s_fk[h];
         p.count = s_cntp[h];
         if constexpr (TOPK) {
           const unsigned long long* top = reinterpret_cast<const unsigned long long*>(s_acc) + e * kMaxTopK;
-          p.mmin = 0;
           p.rep = top[0];
 #pragma unroll
-          for (int a = 0; a < 7; ++a) p.s[a] = top[a];
+          for (int a = 0; a < kMaxTopK - 1; ++a) p.top[a] = top[a + 1];
         } else {
-          p.mmin = s_minp[h];
+          p.sum.mmin = s_minp[h];
+          p.sum.pad = 0;
           p.rep = ((unsigned long long)s_cmaxp[h] << 32) | (unsigned)(~s_gmin[e]);
 #pragma unroll
           for (int a = 0; a < 7; ++a)
-            p.s[a] = ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
-                     s_acc[(2 * a) * kAssignNL + e];
+            p.set_sum(a, ((unsigned long long)s_acc[(2 * a + 1) * kAssignNL + e] << kLoBits) +
+                             s_acc[(2 * a) * kAssignNL + e]);
         }
-        first = file_partial(t, p, s_ek[e], pi);
+        first = file_partial(t, p, slot, s_ek[e], TOPK ? INT_MAX : s_minp[h], pi);
       }
     }
     // one counter update per warp for the cells claimed in it
@@ -1052,9 +1052,9 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
         const Partial P = t.part[p];
         count += P.count;
         rep = max(rep, P.rep);
-        const int sh = P.mmin - mmin;          // shift to the cell's smallest exponent
+        const int sh = P.sum.mmin - mmin;      // shift to the cell's smallest exponent
 #pragma unroll
-        for (int a = 0; a < 7; ++a) S[a] += sh < 64 ? (P.s[a] >> sh) : 0ull;
+        for (int a = 0; a < 7; ++a) S[a] += sh < 64 ? (P.get_sum(a) >> sh) : 0ull;
         p = P.next;
       }
       if (steps > n_part) atomicOr(&t.cnt->error, kErrList);
@@ -1122,8 +1122,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce_topk(const RigDev* __restri
       for (unsigned p = rec.head; p != kSlotNone && steps <= n_part; ++steps) {
         const Partial P = t.part[p];
         count += P.count;
-        for (int a = 0; a < K; ++a) {           // insert P.s[a] into the sorted list
-          unsigned long long key = P.s[a];
+        for (int a = 0; a < K; ++a) {           // insert the tile's key a into the sorted list
+          unsigned long long key = a == 0 ? P.rep : P.top[a - 1];
 #pragma unroll
           for (int q = 0; q < kMaxTopK; ++q) {
             if (q < K && key > top[q]) {
