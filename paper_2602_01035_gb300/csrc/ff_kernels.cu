@@ -536,8 +536,13 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
 
 // ------------------------------------------------------------------ assign step
 constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
-// Distinct cells of a tile with shared-memory accumulators; the members of any further
-// cell (sparse, noisy tiles only) file one single-member partial each.
+// Distinct cells of a tile with shared-memory accumulators.  In a tile with more distinct
+// cells (sparse, noisy tiles only) the cells with two or more members in the tile take the
+// accumulators and every other member files a single-member partial, which is the record
+// the accumulator would have produced for it; if even the multi-member cells are too many,
+// every member files alone.  Both rules depend on the tile's cells alone, never on the
+// order of the insertions, so that every cell's sums, and the fused cloud, are bitwise
+// reproducible.
 constexpr int kAssignNL = kTilePx / 2;
 static_assert(kMaxTopK * 8 <= 14 * 4, "a cell's top-k keys fit in its 14 split-sum words");
 constexpr int kAssignBlocksPerSM = 4;      // registers (64) and shared memory allow four
@@ -634,7 +639,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   float* s_z = reinterpret_cast<float*>(smem + kSmZ);
   float* s_c = reinterpret_cast<float*>(smem + kSmC);
   unsigned* s_rgb = reinterpret_cast<unsigned*>(smem + kSmRGB);
-  __shared__ unsigned s_n, s_base, s_ng;
+  __shared__ unsigned s_n, s_base, s_ng, s_nm;
 
   const RigDev& rig = *rigp;
   int cam, x0, y0;
@@ -902,8 +907,40 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     if (trace && tr.key) tr.key[gi[j]] = has[j] ? fkey[j] : kKeyEmpty;
   }
   __syncthreads();
+  // more cells than accumulators: the multi-member cells take them (see kAssignNL)
+  const bool renumber = s_n > (unsigned)kAssignNL;         // the same in every thread
+  bool all_alone = false;
+  unsigned n_local = s_n;
+  if (renumber) {
+    if (threadIdx.x == 0) s_nm = 0u;
+    __syncthreads();
+    for (int h = threadIdx.x; h < kAssignTS; h += kThreads) {
+      if (s_fk[h] == kSlotNone) continue;
+      int e = kAssignNL;
+      if (s_cntp[h] >= 2u) {
+        e = (int)atomicAdd(&s_nm, 1u);
+        if (e < kAssignNL) {
+          s_ep[e] = (unsigned)h;
+          s_gmin[e] = 0xffffffffu;
+          if constexpr (TOPK) {
+            unsigned long long* top = reinterpret_cast<unsigned long long*>(s_acc) + e * kMaxTopK;
+#pragma unroll
+            for (int q = 0; q < kMaxTopK; ++q) top[q] = 0ull;
+          } else {
+#pragma unroll
+            for (int a = 0; a < 14; ++a) s_acc[a * kAssignNL + e] = 0u;
+          }
+        } else {
+          e = kAssignNL;
+        }
+      }
+      s_fi[h] = e;
+    }
+    __syncthreads();
+    all_alone = s_nm > (unsigned)kAssignNL;
+    n_local = all_alone ? 0u : s_nm;
+  }
   // reserve the tile's partial records now; the index is needed only at the end
-  const unsigned n_local = min(s_n, (unsigned)kAssignNL);
   unsigned base_pi = 0u;
   if (threadIdx.x == 0) base_pi = atomicAdd(&t.cnt->n_partials, n_local);
   // representative: lowest pixel index among the largest C; Eq. 11 sums at the tile's
@@ -912,7 +949,8 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   for (int j = 0; j < 2; ++j) {
     if (!has[j]) continue;
     const int h = hpos[j], e = s_fi[h];
-    const bool alone = e >= kAssignNL;
+    const bool alone = all_alone || e >= kAssignNL;
+    if (renumber && !alone) s_ek[e] = fkey[j];  // every member writes the cell's key
     if constexpr (TOPK) {
       // Sec. II.5(2)a: insert the member into its cell's sorted top-k list; each slot keeps
       // the largest key that reaches it and passes the smaller one down, so the list ends

@@ -111,6 +111,41 @@ def test_sparse_tiles_overflow_the_shared_accumulators(ffmod, oracle_mod):
     assert rep["n_cells_matched"] > 10000
 
 
+def test_overflowing_tiles_are_bitwise_reproducible(ffmod, oracle_mod):
+    """Tiles with more than 256 distinct cells, many of them with two members of unequal
+    weight: which cells of such a tile would get a shared accumulator must not depend on
+    the order of the threads' insertions, so every run gives the same bits."""
+    rig = S.tiny_rig(n=3, width=128, height=64, fx=80.0, fy=80.0)
+    rng = np.random.default_rng(12)
+    z, c, col = [], [], []
+    for _ in range(3):
+        d = rng.integers(500, 40000, size=(64, 128)).astype(np.uint16)
+        paired = (np.arange(64) % 3) != 0
+        d[paired, 1::2] = d[paired, 0::2]            # adjacent pixels at one depth: one cell
+        z.append(d)
+        c.append(rng.uniform(0.61, 1.0, size=(64, 128)).astype(np.float32))
+        col.append(rng.integers(0, 256, size=(64, 128, 3), dtype=np.uint8))
+    fr = S.Frame(z, c, col)
+    params = {"max_level": 0}
+    rep, ref, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr, params)
+    assert rep["n_cells_matched"] > 5000
+    assert (ref["cells"]["count"] >= 2).sum() > 2000
+    for trial in range(3):
+        ff = ffmod.FuseFlow(rig, **params)
+        try:
+            if trial == 1:
+                ff.set_tuning(1, 1, 0)
+            for _ in range(3):
+                o = run_gpu(ff, fr, torch, with_trace=True)
+                assert o["stats"] == ref["stats"]
+                for k in ref["cells"]:
+                    assert np.array_equal(o["cells"][k], ref["cells"][k], equal_nan=True), k
+                for k in ref["trace"]:
+                    assert np.array_equal(o["trace"][k], ref["trace"][k], equal_nan=True), k
+        finally:
+            ff.close()
+
+
 @pytest.mark.parametrize("k", [1, 3, 7])
 def test_top_k_variant(ffmod, oracle_mod, k):
     """Sec. II.5(2)a: each cell fuses only its k most confident members; consistency and

@@ -24,11 +24,20 @@ def ffmod():
     return fuseflow
 
 
+def _rows_differ(x, y):
+    x, y = x.reshape(len(x), -1), y.reshape(len(y), -1)
+    same = (x == y) | (np.isnan(x) & np.isnan(y)) if x.dtype.kind == "f" else x == y
+    return np.flatnonzero(~np.all(same, axis=1))
+
+
 def _same(a, b, with_trace=True):
     assert a["status"] == b["status"]
     assert a["stats"] == b["stats"]
     for k in ("pos", "rgb", "weight", "count", "rep", "key"):
-        assert np.array_equal(a["cells"][k], b["cells"][k], equal_nan=True), k
+        bad = _rows_differ(a["cells"][k], b["cells"][k])
+        detail = [(int(i), a["cells"][k][i].tolist(), b["cells"][k][i].tolist(),
+                   hex(int(a["cells"]["key"][i])), int(a["cells"]["count"][i])) for i in bad[:4]]
+        assert len(bad) == 0, f"{k}: {len(bad)} rows differ, e.g. {detail}"
     if with_trace:
         for k in a["trace"]:
             assert np.array_equal(a["trace"][k], b["trace"][k], equal_nan=True), k
