@@ -1650,6 +1650,96 @@ __global__ void __launch_bounds__(kThreads) k_screen(ScreenArgs a) {
   }
 }
 
+// The same screen for images whose rows start on 16-byte boundaries (every width a
+// multiple of 8, 16-byte aligned buffers): a block covers 8 rows x 256 columns of one
+// camera, a thread 8 consecutive pixels of one row, read and written as 16-byte vectors
+// (two for float32).  The rows above and below come from the neighbouring warps' loads
+// through L1/L2; left and right neighbours from the adjacent lanes, the warp's two outer
+// ones by scalar loads.
+template <typename DT>
+__device__ __forceinline__ void load_row8(const DT* __restrict__ p, DT v[8]) {
+  if constexpr (sizeof(DT) == 2) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { v[2 * k] = (DT)(w[k] & 0xffffu); v[2 * k + 1] = (DT)(w[k] >> 16); }
+  } else {
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = f0.x; v[1] = f0.y; v[2] = f0.z; v[3] = f0.w;
+    v[4] = f1.x; v[5] = f1.y; v[6] = f1.z; v[7] = f1.w;
+  }
+}
+
+template <typename DT>
+__device__ __forceinline__ void store_row8(DT* __restrict__ p, const DT v[8]) {
+  if constexpr (sizeof(DT) == 2) {
+    uint4 u;
+    u.x = (unsigned)v[0] | ((unsigned)v[1] << 16);
+    u.y = (unsigned)v[2] | ((unsigned)v[3] << 16);
+    u.z = (unsigned)v[4] | ((unsigned)v[5] << 16);
+    u.w = (unsigned)v[6] | ((unsigned)v[7] << 16);
+    *reinterpret_cast<uint4*>(p) = u;
+  } else {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+template <typename DT>
+__device__ __forceinline__ DT shfl_depth(DT v, int delta, bool up) {
+  if constexpr (sizeof(DT) == 2) {
+    const unsigned u = up ? __shfl_up_sync(0xffffffffu, (unsigned)v, delta)
+                          : __shfl_down_sync(0xffffffffu, (unsigned)v, delta);
+    return (DT)u;
+  } else {
+    return up ? __shfl_up_sync(0xffffffffu, v, delta) : __shfl_down_sync(0xffffffffu, v, delta);
+  }
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_screen_rows(ScreenArgs a) {
+  const int cam = blockIdx.z;
+  const int W = a.W[cam], H = a.H[cam];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.y * 8 + warp;
+  const int x0 = blockIdx.x * 256 + lane * 8;
+  const bool active = y < H && x0 < W;              // W % 8 == 0: all 8 pixels inside
+  const DT* __restrict__ in = static_cast<const DT*>(a.in[cam]);
+  DT v[8], up[8], dn[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = (DT)0; up[k] = (DT)0; dn[k] = (DT)0; }
+  if (active) {
+    const size_t row = (size_t)y * (size_t)W + (size_t)x0;
+    load_row8<DT>(in + row, v);
+    if (y > 0) load_row8<DT>(in + row - W, up);
+    if (y + 1 < H) load_row8<DT>(in + row + W, dn);
+  }
+  // neighbours across the thread's 8-pixel group: adjacent lanes, or a scalar load at the
+  // warp's edges (a sample outside the image counts as invalid: it never screens)
+  DT left = shfl_depth<DT>(v[7], 1, true), right = shfl_depth<DT>(v[0], 1, false);
+  if (lane == 0) left = (active && x0 > 0) ? __ldg(in + (size_t)y * W + x0 - 1) : (DT)0;
+  if (lane == 31) right = (active && x0 + 8 < W) ? __ldg(in + (size_t)y * W + x0 + 8) : (DT)0;
+  if (x0 + 8 >= W) right = (DT)0;
+  if (!active) return;
+  const float rel = a.edge_rel;
+  DT o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    bool keep = screen_keep<DT>(v[k], a.min_u, a.max_u);
+    if (keep && rel > 0.0f) {
+      const float z = Depth<DT>::z(v[k]), thr = __fmul_rn(rel, z);
+      const DT nb[4] = {k > 0 ? v[k - 1] : left, k < 7 ? v[k + 1] : right, up[k], dn[k]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (screen_keep<DT>(nb[q], a.min_u, a.max_u) && fabsf(__fsub_rn(z, Depth<DT>::z(nb[q]))) > thr)
+          keep = false;
+    }
+    o[k] = keep ? v[k] : (DT)0;
+  }
+  store_row8<DT>(static_cast<DT*>(a.out[cam]) + (size_t)y * W + x0, o);
+}
+
 // Dynamic shared memory limit of the assign kernels for one depth type, set once (the
 // first call comes from context creation, outside any stream capture).
 template <typename DT>
@@ -1790,10 +1880,24 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
 }
 
 cudaError_t launch_screen(const ScreenArgs& a, bool depth_f32, long long max_px, cudaStream_t s) {
-  const unsigned bx = (unsigned)std::min<long long>((max_px + kThreads - 1) / kThreads, 4096);
-  const dim3 grid(std::max(1u, bx), a.n_cams);
-  if (depth_f32) k_screen<float><<<grid, kThreads, 0, s>>>(a);
-  else k_screen<uint16_t><<<grid, kThreads, 0, s>>>(a);
+  bool rows = true;                                   // 16-byte rows: the vector kernel
+  int max_w = 1, max_h = 1;
+  for (int i = 0; i < a.n_cams; ++i) {
+    rows = rows && a.W[i] % 8 == 0 && (reinterpret_cast<uintptr_t>(a.in[i]) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(a.out[i]) & 15) == 0;
+    max_w = std::max(max_w, a.W[i]);
+    max_h = std::max(max_h, a.H[i]);
+  }
+  if (rows) {
+    const dim3 grid((unsigned)((max_w + 255) / 256), (unsigned)((max_h + 7) / 8), (unsigned)a.n_cams);
+    if (depth_f32) k_screen_rows<float><<<grid, kThreads, 0, s>>>(a);
+    else k_screen_rows<uint16_t><<<grid, kThreads, 0, s>>>(a);
+  } else {
+    const unsigned bx = (unsigned)std::min<long long>((max_px + kThreads - 1) / kThreads, 4096);
+    const dim3 grid(std::max(1u, bx), a.n_cams);
+    if (depth_f32) k_screen<float><<<grid, kThreads, 0, s>>>(a);
+    else k_screen<uint16_t><<<grid, kThreads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
