@@ -250,7 +250,7 @@ const char *fuseflow_stage_name(int stage);
  *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
  *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
  *                   depth rows into L2; 0 turns the prefetch off
- * fuseflow_create picks count_chunks for one wave of three count blocks per SM (at most 8),
+ * fuseflow_create picks count_chunks for one wave of four count blocks per SM (at most 6),
  * emit_blocks = 8 blocks per SM and prefetch_tiles = one wave of assign blocks. */
 typedef struct fuseflow_tuning {
   int32_t count_chunks;

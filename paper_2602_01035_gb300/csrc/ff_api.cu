@@ -365,13 +365,13 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   {
-    // several 2048-pixel chunks per count block: one wave of 3 blocks per SM, but at most 8
-    // chunks, since a block's table of coarse cells (2048 entries) spills to the global
-    // table when one block covers too much of the scene
+    // several 2048-pixel chunks per count block: one wave of 4 blocks per SM (the kernel's
+    // residency), but at most 6 chunks, since a block's table of coarse cells (2048
+    // entries) spills to the global table when one block covers too much of the scene
     long long total_chunks = 0;
     for (int i = 0; i < n_cams; ++i) total_chunks += ((long long)intr[i].width * intr[i].height + 2047) / 2048;
-    const long long per = (total_chunks + 3ll * sms - 1) / (3ll * sms);
-    ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(8, per));
+    const long long per = (total_chunks + 4ll * sms - 1) / (4ll * sms);
+    ctx->geo.count_chunks = (int)std::max<long long>(1, std::min<long long>(6, per));
     ctx->max_chunks = (max_px + 2047) / 2048;
     ctx->geo.count_blocks_x = (int)((ctx->max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
@@ -877,7 +877,7 @@ struct Autotuner {
     long long total_chunks = 0;
     for (int i = 0; i < ctx->n_cams; ++i)
       total_chunks += ((long long)ctx->intr[i].width * ctx->intr[i].height + 2047) / 2048;
-    std::vector<int> chunks = {2, 4, 8, 16};
+    std::vector<int> chunks = {2, 4, 6, 8, 16};
     for (int b : {1, 2, 3, 4, 6, 8}) {
       const long long per = (total_chunks + (long long)b * sms - 1) / ((long long)b * sms);
       chunks.push_back((int)std::max<long long>(1, std::min<long long>(64, per)));

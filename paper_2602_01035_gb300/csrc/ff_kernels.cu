@@ -350,7 +350,7 @@ __device__ __forceinline__ void count_add(const Tables& t, unsigned long long* s
 }
 
 template <typename DT>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 4)
 k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
         int blocks_x, int chunks) {
   constexpr int TS = 2048;                                      // block table of coarse keys
@@ -379,21 +379,18 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   unsigned nv = 0, ng = 0, noor = 0;
   float fmn[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
   float fmx[3] = {__int_as_float(0xff800000), __int_as_float(0xff800000), __int_as_float(0xff800000)};
-  DT dv[kCountPx];
-  float cv[kCountPx];
   long long pn = (c0 * kThreads + threadIdx.x) * kCountPx;
-  if (!idle && pn < npx) load8<DT>(dep, cf, pn, npx, dv, cv);
   int y = (int)((unsigned)pn / (unsigned)C.W);                  // W H <= 2^30
   int x = (int)((unsigned)pn - (unsigned)y * (unsigned)C.W);
+  // no prefetch of the next chunk: registers stay under 64, and four resident blocks per
+  // SM hide the load latency better than a second set of eight samples per thread did
   for (int ch = 0; ch < (idle ? 0 : chunks); ++ch) {
     const long long pc = pn;
     if ((c0 + ch) * kCountBlockPx >= npx) break;                 // uniform over the block
     DT dcur[kCountPx];
     float ccur[kCountPx];
-#pragma unroll
-    for (int k = 0; k < kCountPx; ++k) { dcur[k] = dv[k]; ccur[k] = cv[k]; }
-    pn = pc + kCountBlockPx;                                      // prefetch the next chunk
-    if (ch + 1 < chunks && pn < npx) load8<DT>(dep, cf, pn, npx, dv, cv);
+    if (pc < npx) load8<DT>(dep, cf, pc, npx, dcur, ccur);
+    pn = pc + kCountBlockPx;
     // Sec. II.5(1)c density estimate. Runs of equal coarse cells along the thread's
     // pixels: the first run (if the thread has several) and the last run are kept, the
     // ones between go to the block table at once (rare: a cell spans ~70 pixels here).
