@@ -1719,18 +1719,38 @@ __global__ void __launch_bounds__(kThreads) k_screen_rows(ScreenArgs a) {
   if (lane == 31) right = (active && x0 + 8 < W) ? __ldg(in + (size_t)y * W + x0 + 8) : (DT)0;
   if (x0 + 8 >= W) right = (DT)0;
   if (!active) return;
+  // valid and within the bounds as two compares: z >= lo and z <= hi, with lo the lower
+  // bound or the smallest positive float (so that 0, negatives and NaN fail) and hi the
+  // upper bound or the largest finite float (so that +inf fails); the same decision as
+  // screen_keep (no flush of subnormals in this build)
+  const float lo = a.min_u > 0.0f ? a.min_u : __int_as_float(1);
+  const float hi = a.max_u > 0.0f ? a.max_u : __int_as_float(0x7f7fffff);
+  float zc[8], zu[8], zd[8];
+  bool oc[8], ou[8], od[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    zc[k] = Depth<DT>::z(v[k]);
+    zu[k] = Depth<DT>::z(up[k]);
+    zd[k] = Depth<DT>::z(dn[k]);
+    oc[k] = zc[k] >= lo && zc[k] <= hi;
+    ou[k] = zu[k] >= lo && zu[k] <= hi;
+    od[k] = zd[k] >= lo && zd[k] <= hi;
+  }
+  const float zl = Depth<DT>::z(left), zr = Depth<DT>::z(right);
+  const bool ol = zl >= lo && zl <= hi, orr = zr >= lo && zr <= hi;
   const float rel = a.edge_rel;
   DT o[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    bool keep = screen_keep<DT>(v[k], a.min_u, a.max_u);
-    if (keep && rel > 0.0f) {
-      const float z = Depth<DT>::z(v[k]), thr = __fmul_rn(rel, z);
-      const DT nb[4] = {k > 0 ? v[k - 1] : left, k < 7 ? v[k + 1] : right, up[k], dn[k]};
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (screen_keep<DT>(nb[q], a.min_u, a.max_u) && fabsf(__fsub_rn(z, Depth<DT>::z(nb[q]))) > thr)
-          keep = false;
+    bool keep = oc[k];
+    if (rel > 0.0f) {
+      const float z = zc[k], thr = __fmul_rn(rel, z);
+      const float zw = k > 0 ? zc[k - 1] : zl, ze = k < 7 ? zc[k + 1] : zr;
+      const bool ow = k > 0 ? oc[k - 1] : ol, oe = k < 7 ? oc[k + 1] : orr;
+      const bool jump = (ow && fabsf(__fsub_rn(z, zw)) > thr) || (oe && fabsf(__fsub_rn(z, ze)) > thr) ||
+                        (ou[k] && fabsf(__fsub_rn(z, zu[k])) > thr) ||
+                        (od[k] && fabsf(__fsub_rn(z, zd[k])) > thr);
+      keep = keep && !jump;
     }
     o[k] = keep ? v[k] : (DT)0;
   }
