@@ -73,8 +73,9 @@ typedef struct {
                                (ties to the lowest pixel index), with consistency computed
                                for those alone; 0 = every member (default); at most 7 */
     int64_t max_cells;      /* output capacity in cells; 0 = max(65536, pixels / 8) */
-    /* Depth preprocessing D^r of Eq. 8 ("filtered or screened"; the paper gives no rule, so
-     * this one is stated here).  A screened-out pixel counts as invalid everywhere: in the
+    /* Depth preprocessing D^r of Eq. 8 (the paper leaves the rule open, naming filtering and
+     * screening as examples, so this one is stated here).  A screened-out pixel counts as
+     * invalid everywhere: in the
      * back-projection and in the other views' consistency gathers of Eq. 5.  All three are
      * off by default (<= 0), and then D^r = D.  Decisions are taken in float32 on depth
      * units: bounds b_u = (float)(b_m / depth_scale); a valid depth d is kept iff

@@ -22,7 +22,7 @@
  *    edge s0 / 2^l.  Points whose finest-level index leaves [-2^19, 2^19) are dropped.
  *  - Sec. II.5(2)a keeps every gated member of a cell in the fusion; the representative
  *    is the member of largest C, ties to the lowest pixel index.
- *  - Eq. 8's D^r ("filtered or screened") has no stated rule; orc_screen_depth gives the
+ *  - Eq. 8's preprocessed depth D^r has no stated rule; orc_screen_depth gives the
  *    one read here (a depth range and a relative-jump screen against 4-neighbours), off
  *    by default so that D^r = D.
  *  - Eq. 11 is read as the normalised weighted mean over the cell's members (positions

@@ -93,7 +93,8 @@ void orc_default_params(orc_params *p);
 /* Static neighbour table: for each camera the K-1 other cameras used in Eq. 7. */
 int orc_neighbours(const orc_camera *cams, int32_t n_cams, int32_t k_views, int32_t *out);
 
-/* D^r of Eq. 8, "depth after necessary preprocessing (e.g. filtered or screened)".  The
+/* D^r of Eq. 8: the depth after a preprocessing step that the paper leaves open (its
+ * examples are filtering and screening).  The
  * paper states no rule; the one read here: in depth units, with every comparison in
  * float32 (the same decision the GPU takes), bounds b_u = (float)(b_m / depth_scale);
  * a valid sample d (> 0, finite) is kept iff d >= min_u (bound set) and d <= max_u (bound

@@ -1,4 +1,4 @@
-"""Pins of the oracle's depth screen D^r (Eq. 8, "filtered or screened"; the rule is stated
+"""Pins of the oracle's depth screen D^r (the preprocessed depth of Eq. 8; the rule is stated
 with orc_screen_depth) against closed forms on constructed images, and of its wiring into
 the frame: a frame fused with a screen set equals the frame fused, unscreened, from the
 screened images."""
