@@ -22,6 +22,7 @@
 // Every reduction of the frame is order-independent (integer counts, max, min and
 // fixed-point sums), so its output is bitwise reproducible.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdint>
 
@@ -1757,12 +1758,16 @@ __global__ void __launch_bounds__(kThreads) k_screen_rows(ScreenArgs a) {
   store_row8<DT>(static_cast<DT*>(a.out[cam]) + (size_t)y * W + x0, o);
 }
 
-// Dynamic shared memory limit of the assign kernels for one depth type, set once (the
-// first call comes from context creation, outside any stream capture).
+// Dynamic shared memory limit of the assign kernels for one depth type, set once per device
+// (the first call comes from context creation, outside any stream capture).  The attribute
+// call is idempotent, so two host threads that race here only repeat it.
 template <typename DT>
 cudaError_t set_assign_attributes() {
-  static bool attr_set = false;
-  if (attr_set) return cudaSuccess;
+  static std::atomic<unsigned long long> done{0ull};       // one bit per device (< 64)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   const int sm = (int)assign_smem(kMaxK1);
   cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess)
@@ -1771,7 +1776,7 @@ cudaError_t set_assign_attributes() {
     e = cudaFuncSetAttribute(k_assign<DT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_assign<DT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) attr_set = true;
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
   return e;
 }
 
