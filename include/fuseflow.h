@@ -155,7 +155,8 @@ int fuseflow_fuse_frame(fuseflow_ctx *ctx, const void *const *depth, const float
 /* A fuse call recorded once as a CUDA graph, for callers whose input images live in the
  * same device buffers every frame (a capture loop that refills them): replaying it with
  * fuseflow_graph_launch is the same as calling fuseflow_fuse_frame with the pointers
- * given here, whose contents may change between launches, at one launch instead of seven.
+ * given here, whose contents may change between launches, at one launch instead of seven
+ * (eight with a depth screen set).
  * The graph keeps the context's launch geometry and trace registration as they were at
  * creation; results do not depend on the geometry.  It uses the context's tables, so
  * launches of graphs and fuse calls of one context must be ordered (one stream), and
@@ -237,8 +238,9 @@ int fuseflow_get_neighbours(const fuseflow_ctx *ctx, int32_t *out, int32_t *k_mi
  * events between its stages on its own stream (a ring of the last 1024 frames).
  * fuseflow_read_stage_times waits for the last recorded event, writes the summed
  * milliseconds of each of the FUSEFLOW_N_STAGES stages to ms[] and the number of frames
- * to *n_frames, then resets the ring.  Stages: 0 clear, 1 count (a, c2), 2 assign
- * (b, c, d per tile), 3 reduce (d per cell), 4 scan, 5 emit. */
+ * to *n_frames, then resets the ring.  Stages: 0 clear (and the depth screen when one is
+ * set), 1 count (a, c2), 2 assign (b, c, d per tile), 3 reduce (d per cell), 4 scan,
+ * 5 emit. */
 #define FUSEFLOW_N_STAGES 6
 int fuseflow_enable_stage_timing(fuseflow_ctx *ctx, int enable);
 int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
