@@ -35,7 +35,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kCountPx = 8;                       // pixels per thread in the count step
 constexpr int kCountBlockPx = kThreads * kCountPx;
-constexpr int kTileW = 32, kTileH = 16;           // assign/accum tile: 8 warps x 2 rows
+constexpr int kTileW = 32, kTileH = 16;           // assign/accum tile: one warp per 2 rows
 constexpr int kTilePx = kTileW * kTileH;
 constexpr int kPrayPerView = 2 * kTileW + 2 * kTileH;   // staged pair-ray float4 per view
 constexpr int kMaxProbe = 1 << 14;
@@ -543,10 +543,14 @@ constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pix
 // reproducible.
 constexpr int kAssignNL = kTilePx / 2;
 static_assert(kMaxTopK * 8 <= 14 * 4, "a cell's top-k keys fit in its 14 split-sum words");
-constexpr int kAssignBlocksPerSM = 4;      // registers (64) and shared memory allow four
+constexpr int kAssignThreads = 16 * kTileH;        // one warp per two rows of the tile
+constexpr int kAssignWarps = kAssignThreads / 32;
+// registers (64 a thread) and shared memory allow this many blocks of a 32x16 tile
+constexpr int kAssignBlocksPerSM = 4 * 256 / kAssignThreads;
+constexpr int kConstWords = (int)((sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev))) / 4 +
+                                  kAssignThreads - 1) / kAssignThreads;
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
-static_assert(sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev)) <= 2 * 4 * kThreads,
-              "two words per thread copy a block's constants");
+static_assert(kConstWords <= 4, "a few words per thread copy a block's constants");
 constexpr size_t kSmBC = 0;
 // per hash position (kAssignTS): cell slot, entry index, smallest weight exponent, largest
 // ordered C, member count; the last four are contiguous so that one loop clears them
@@ -619,7 +623,7 @@ __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, in
 // each cell's top-k members by C (packed (ordered(C) << 32) | ~g keys) instead of weights;
 // the consistency and weights of those members are computed per cell by k_reduce_topk.
 template <typename DT, bool TOPK, bool TRACE>
-__global__ void __launch_bounds__(kThreads, kAssignBlocksPerSM)
+__global__ void __launch_bounds__(kAssignThreads, kAssignBlocksPerSM)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m, TileIndex ti) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -671,10 +675,10 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   constexpr int kNbAt = (int)(offsetof(BlockConst, nb) / 4), kPairAt = (int)(offsetof(BlockConst, pair) / 4);
   const int n_cw = kCamW + k1 * (kPairW + kCamW);
   const int* gsrc = reinterpret_cast<const int*>(&t.bconst[cam]);
-  int cwv[2], cwi[2];
+  int cwv[kConstWords], cwi[kConstWords];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int w = threadIdx.x + r * kThreads;
+  for (int r = 0; r < kConstWords; ++r) {
+    const int w = threadIdx.x + r * kAssignThreads;
     cwi[r] = w < kCamW ? w
            : w < kCamW + k1 * kPairW ? kPairAt + (w - kCamW)
            : w < n_cw ? kNbAt + (w - kCamW - k1 * kPairW) : -1;
@@ -682,14 +686,14 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   }
   // the tile's pair rays (Eq. 4): per view, A of its 32 columns and B of its 16 rows, each
   // as two float4 planes: [A first halves | A second halves | B first | B second]
-  constexpr int kPrayLoads = (kMaxK1 * kPrayPerView + kThreads - 1) / kThreads;
+  constexpr int kPrayLoads = (kMaxK1 * kPrayPerView + kAssignThreads - 1) / kAssignThreads;
   float4 prv[kPrayLoads];
   int pri[kPrayLoads];
   {
     const int Wp = W, Hp = H;
 #pragma unroll
     for (int r = 0; r < kPrayLoads; ++r) {
-      const int idx = threadIdx.x + r * kThreads;
+      const int idx = threadIdx.x + r * kAssignThreads;
       pri[r] = -1;
       prv[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       if (TOPK || idx >= k1 * kPrayPerView) continue;
@@ -715,7 +719,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   bool inimg[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const int x = td.x0 + lane, y = td.y0 + warp + 8 * k;
+    const int x = td.x0 + lane, y = td.y0 + warp + kAssignWarps * k;
     inimg[k] = x < W && y < H;
     Dk[k] = (DT)0;
     ckv[k] = 0.0f;
@@ -732,14 +736,14 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   }
   int* sdst = reinterpret_cast<int*>(&bc);
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+  for (int r = 0; r < kConstWords; ++r)
     if (cwi[r] >= 0) sdst[cwi[r]] = cwv[r];
   float4* s_pr = reinterpret_cast<float4*>(smem + kSmPR);
 #pragma unroll
   for (int r = 0; r < kPrayLoads; ++r)
     if (pri[r] >= 0) s_pr[pri[r]] = prv[r];
   // clear the per-position arrays: slot none, exponent INT_MAX, largest C 0, count 0
-  for (int i = threadIdx.x; i < kAssignTS; i += kThreads) {
+  for (int i = threadIdx.x; i < kAssignTS; i += kAssignThreads) {
     const unsigned v = i < kAssignTS / 4 ? kSlotNone : i < kAssignTS / 2 ? (unsigned)INT_MAX : 0u;
     reinterpret_cast<uint4*>(smem + kSmFK)[i] = make_uint4(v, v, v, v);
   }
@@ -753,7 +757,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   // below is order-independent), so that the per-point work runs on full warps
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const int row = warp + 8 * k;
+    const int row = warp + kAssignWarps * k;
     bool gated = false;
     if (inimg[k]) {
       gated = Depth<DT>::valid(Dk[k]) && (!rig.use_conf || ckv[k] > rig.tau);
@@ -785,7 +789,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   // the second point's coarse record: start its lookup now (into L1), so that it arrives
   // while the first point is processed
   {
-    const int i = threadIdx.x + kThreads;
+    const int i = threadIdx.x + kAssignThreads;
     if (i < n_g) {
       const int pid = s_pid[i];
       const int x = td.x0 + (pid & (kTileW - 1)), y = td.y0 + pid / kTileW;
@@ -809,7 +813,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   unsigned long long fkey[2] = {kKeyEmpty, kKeyEmpty};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const int i = threadIdx.x + j * kThreads;
+    const int i = threadIdx.x + j * kAssignThreads;
     if (i >= n_g) continue;
     const int pid = s_pid[i];
     const int x = td.x0 + (pid & (kTileW - 1)), y = td.y0 + pid / kTileW;
@@ -912,7 +916,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   if (renumber) {
     if (threadIdx.x == 0) s_nm = 0u;
     __syncthreads();
-    for (int h = threadIdx.x; h < kAssignTS; h += kThreads) {
+    for (int h = threadIdx.x; h < kAssignTS; h += kAssignThreads) {
       if (s_fk[h] == kSlotNone) continue;
       int e = kAssignNL;
       if (s_cntp[h] >= 2u) {
@@ -980,7 +984,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
     if (!alone && cord[j] == s_cmaxp[h]) atomicMin(&s_gmin[e], (unsigned)gi[j]);
     const int sh = alone ? 0 : mexp[j] - s_minp[h];
     const float w = sh > 62 ? 0.0f : __fmul_rn(mu[j], pow2f(kFixShift - sh));
-    const unsigned rgb = s_rgb[threadIdx.x + j * kThreads];
+    const unsigned rgb = s_rgb[threadIdx.x + j * kAssignThreads];
     float v[7];
     v[0] = w;
 #pragma unroll
@@ -1021,7 +1025,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   if (threadIdx.x == 0) s_base = base_pi;
   __syncthreads();
   // one partial record per (tile, cell), pushed onto its cell's list
-  for (int e0 = 0; e0 < (int)n_local; e0 += kThreads) {
+  for (int e0 = 0; e0 < (int)n_local; e0 += kAssignThreads) {
     const int e = e0 + threadIdx.x;
     bool first = false;
     unsigned slot = 0u;
@@ -1807,19 +1811,19 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
   const bool traced = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
   if (geo.top_k) {
     if (traced)
-      k_assign<DT, true, true><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
+      k_assign<DT, true, true><<<t.n_tiles, kAssignThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
                                                                          (float)out.unit_m, geo.tiles);
     else
-      k_assign<DT, true, false><<<t.n_tiles, kThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
+      k_assign<DT, true, false><<<t.n_tiles, kAssignThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
                                                                           (float)out.unit_m, geo.tiles);
     mark(3);
     k_reduce_topk<DT><<<geo.emit_blocks, kThreads, 0, s>>>(rig, rays, fp, t, out);
   } else {
     if (traced)
-      k_assign<DT, false, true><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(
+      k_assign<DT, false, true><<<t.n_tiles, kAssignThreads, assign_smem(geo.tiles.k1), s>>>(
           rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
     else
-      k_assign<DT, false, false><<<t.n_tiles, kThreads, assign_smem(geo.tiles.k1), s>>>(
+      k_assign<DT, false, false><<<t.n_tiles, kAssignThreads, assign_smem(geo.tiles.k1), s>>>(
           rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
     mark(3);
     k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
