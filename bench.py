@@ -235,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
 
     def tuned(ctx_obj):
         g = tuning["chosen"]
-        ctx_obj.set_tuning(g["count_chunks"], g["emit_blocks"], g["prefetch_tiles"])
+        ctx_obj.set_tuning(g["count_chunks"], g["emit_blocks"], g["prefetch_tiles"], g["programmatic"])
         return ctx_obj
 
     def step():

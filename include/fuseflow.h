@@ -253,13 +253,19 @@ const char *fuseflow_stage_name(int stage);
  *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
  *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
  *                   depth rows into L2; 0 turns the prefetch off
+ *   programmatic    1: each kernel of a frame after the first is launched with
+ *                   programmatic stream serialization, so that its blocks start while the
+ *                   previous kernel's last blocks finish (they wait for its results on the
+ *                   device); 0: plain stream order.  Stage timing always uses plain order.
  * fuseflow_create picks count_chunks for one wave of four count blocks per SM (at most 6),
- * emit_blocks = 8 blocks per SM and prefetch_tiles = one wave of assign blocks. */
+ * emit_blocks = 8 blocks per SM, prefetch_tiles = one wave of assign blocks, and
+ * programmatic = 1 for rigs of fewer than 2^21 pixels (where the kernel boundaries are a
+ * large share of the frame), 0 otherwise. */
 typedef struct fuseflow_tuning {
   int32_t count_chunks;
   int32_t emit_blocks;
   int32_t prefetch_tiles;
-  int32_t reserved;           /* 0 */
+  int32_t programmatic;       /* 0 or 1 */
 } fuseflow_tuning;
 
 /* Reads (get) or replaces (set) the context's launch geometry.  set returns INVALID_ARG,
@@ -271,7 +277,7 @@ int fuseflow_set_tuning(fuseflow_ctx *ctx, const fuseflow_tuning *in);
 
 /* Autotuner of the launch geometry.  Fuses the given frame (DEVICE inputs as for
  * fuseflow_fuse_frame) repeatedly on `stream` under candidate settings, one knob at a
- * time (count_chunks, then emit_blocks, then prefetch_tiles; coordinate descent from
+ * time (count_chunks, emit_blocks, prefetch_tiles, then programmatic; coordinate descent from
  * the context's current setting), and keeps a candidate only when the median of `reps`
  * timed frames (CUDA events on `stream`, L2 flushed before each frame by writing a
  * scratch buffer of twice the L2 size) is at least 1 % below the best so far.  The

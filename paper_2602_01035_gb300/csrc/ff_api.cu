@@ -376,6 +376,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     ctx->geo.count_blocks_x = (int)((ctx->max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
   ctx->geo.emit_blocks = std::max(1, sms * 8);
+  ctx->geo.pdl = off < (1ll << 21) ? 1 : 0;
 
   // ---------------------------------------------------------------- device memory
   int status = FUSEFLOW_OK;
@@ -802,6 +803,7 @@ static void apply_tuning(fuseflow_ctx* ctx, const fuseflow_tuning& tu) {
   ctx->tab.n_bstats = ctx->geo.count_blocks_x * ctx->n_cams;
   ctx->geo.emit_blocks = tu.emit_blocks;
   ctx->geo.tiles.ahead = tu.prefetch_tiles == 0 ? kNoPrefetch : std::min(tu.prefetch_tiles, kNoPrefetch);
+  ctx->geo.pdl = tu.programmatic;
 }
 
 // Coordinate descent over the launch geometry, timing whole frames on one stream.
@@ -898,6 +900,11 @@ struct Autotuner {
       c.prefetch_tiles = a;
       if ((st = consider(c)) != FUSEFLOW_OK) return st;
     }
+    {
+      fuseflow_tuning c = best;
+      c.programmatic = 1 - best.programmatic;
+      if ((st = consider(c)) != FUSEFLOW_OK) return st;
+    }
     // both settings timed again back to back, so that clocks drift into neither
     if ((st = time_setting(start, &start_us)) != FUSEFLOW_OK) return st;
     if ((st = time_setting(best, &best_us)) != FUSEFLOW_OK) return st;
@@ -914,13 +921,13 @@ int fuseflow_get_tuning(const fuseflow_ctx* ctx, fuseflow_tuning* out) {
   out->count_chunks = ctx->geo.count_chunks;
   out->emit_blocks = ctx->geo.emit_blocks;
   out->prefetch_tiles = ctx->geo.tiles.ahead >= kNoPrefetch ? 0 : ctx->geo.tiles.ahead;
-  out->reserved = 0;
+  out->programmatic = ctx->geo.pdl;
   return FUSEFLOW_OK;
 }
 
 int fuseflow_set_tuning(fuseflow_ctx* ctx, const fuseflow_tuning* in) {
   if (!ctx || !in || in->count_chunks < 1 || in->count_chunks > 64 || in->emit_blocks < 1 ||
-      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || in->reserved != 0)
+      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || (in->programmatic != 0 && in->programmatic != 1))
     return FUSEFLOW_ERR_INVALID_ARG;
   apply_tuning(ctx, *in);
   return FUSEFLOW_OK;
@@ -1156,6 +1163,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   geo.emit_blocks = std::max(1, sms * 8);
+  geo.pdl = 1;                                         // at most 2^19 pixels: small frames
   Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
   t.n_min = params->n_min;
   t.max_level = params->max_level;

@@ -78,7 +78,17 @@ __device__ __forceinline__ unsigned coarse_lvbase(const Tables& t, unsigned long
 // Sec. II.5(1)d for every coarse cell once all counts are in: its level l and a range of
 // 8^l dense cell slots.  Ranges are claimed with one atomic per warp (an inclusive scan of
 // the sizes inside the warp), so their placement depends on scheduling; no result does.
+// Programmatic dependent launch between the kernels of one frame: each kernel lets the next
+// one start launching as soon as all of its own blocks are running (pdl_release), and a
+// kernel waits for the previous one to complete, its memory visible, before it touches
+// anything that one (or any earlier kernel of the frame) wrote (pdl_wait).  Outside such a
+// launch both are no-ops.
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __global__ void __launch_bounds__(kThreads) k_levels(Tables t) {
+  pdl_release();
+  pdl_wait();
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
   const int lane = threadIdx.x & 31;
   const unsigned long long cap = t.max_slots;
@@ -354,6 +364,7 @@ template <typename DT>
 __global__ void __launch_bounds__(kThreads, 4)
 k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
         int blocks_x, int chunks) {
+  pdl_release();
   constexpr int TS = 2048;                                      // block table of coarse keys
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
@@ -626,6 +637,7 @@ template <typename DT, bool TOPK, bool TRACE>
 __global__ void __launch_bounds__(kAssignThreads, kAssignBlocksPerSM)
 k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
          TraceDev tr, float unit_m, TileIndex ti) {
+  pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
   unsigned* s_fk = reinterpret_cast<unsigned*>(smem + kSmFK);
@@ -785,6 +797,9 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   __syncthreads();
   const int n_g = (int)s_ng;
   const CamDev& C = bc.cam;
+  // everything above read only the frame's inputs and the context's constants; the coarse
+  // table (count and level steps) and every table written below need the earlier kernels
+  pdl_wait();
 
   // the second point's coarse record: start its lookup now (into L1), so that it arrives
   // while the first point is processed
@@ -1074,6 +1089,8 @@ __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
+  pdl_release();
+  pdl_wait();
   const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
   const unsigned n_part = min(t.cnt->n_partials, t.max_partials);
@@ -1145,6 +1162,8 @@ template <typename DT>
 __global__ void __launch_bounds__(kThreads) k_reduce_topk(const RigDev* __restrict__ rigp,
                                                           const float2* __restrict__ rays,
                                                           FramePtrs fp, Tables t, OutDev out) {
+  pdl_release();
+  pdl_wait();
   const RigDev& rig = *rigp;
   const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
@@ -1290,6 +1309,8 @@ __global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
   __shared__ unsigned long long s_l[3][32];
   __shared__ unsigned s_b[6][32];
   __shared__ bool s_last;
+  pdl_release();
+  pdl_wait();
   const long long w = (long long)blockIdx.x * 1024 + threadIdx.x;
   const unsigned v = (w < t.n_words) ? __popc(t.bitmap[w]) : 0u;
   unsigned total;
@@ -1378,6 +1399,8 @@ __global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
 
 // ------------------------------------------------------------------ emit
 __global__ void __launch_bounds__(kThreads) k_emit(Tables t, OutDev out) {
+  pdl_release();
+  pdl_wait();
   const unsigned n_cells = (unsigned)min((long long)min(t.cnt->n_cells, t.max_slots), out.max_cells);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
     const CellOut c = t.staged[i];
@@ -1784,6 +1807,24 @@ cudaError_t set_assign_attributes() {
   return e;
 }
 
+// Launch of one of the frame's kernels; pdl: programmatic stream serialization with the
+// kernel before it on the stream (the kernel must call pdl_wait before using its results).
+template <typename... P, typename... A>
+cudaError_t launch_k(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename DT>
 cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp_in, const Tables& t,
                          const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
@@ -1804,34 +1845,37 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
     if ((err = launch_screen(a, sizeof(DT) == 4, geo.max_px, s)) != cudaSuccess) return err;
   }
   mark(1);
-  k_count<DT><<<dim3(geo.count_blocks_x, geo.n_cams), kThreads, 0, s>>>(rig, rays, fp, t, geo.count_blocks_x,
-                                                                       geo.count_chunks);
-  k_levels<<<geo.emit_blocks, kThreads, 0, s>>>(t);
+  // programmatic launches between the frame's kernels when the geometry asks for them,
+  // never while stage events are recorded between them
+  const bool pdl = geo.pdl && ev == nullptr;
+  const float um = (float)out.unit_m;
+  if ((err = launch_k(false, k_count<DT>, dim3(geo.count_blocks_x, geo.n_cams), dim3(kThreads), 0, s, rig, rays,
+                      fp, t, geo.count_blocks_x, geo.count_chunks)) != cudaSuccess ||
+      (err = launch_k(pdl, k_levels, dim3(geo.emit_blocks), dim3(kThreads), 0, s, t)) != cudaSuccess)
+    return err;
   mark(2);
   const bool traced = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
+  const dim3 tiles(t.n_tiles), at(kAssignThreads), eb(geo.emit_blocks), th(kThreads);
   if (geo.top_k) {
-    if (traced)
-      k_assign<DT, true, true><<<t.n_tiles, kAssignThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
-                                                                         (float)out.unit_m, geo.tiles);
-    else
-      k_assign<DT, true, false><<<t.n_tiles, kAssignThreads, assign_smem(0), s>>>(rig, rays, fp, t, tr,
-                                                                          (float)out.unit_m, geo.tiles);
+    err = traced ? launch_k(pdl, k_assign<DT, true, true>, tiles, at, assign_smem(0), s, rig, rays, fp, t, tr, um,
+                            geo.tiles)
+                 : launch_k(pdl, k_assign<DT, true, false>, tiles, at, assign_smem(0), s, rig, rays, fp, t, tr, um,
+                            geo.tiles);
+    if (err != cudaSuccess) return err;
     mark(3);
-    k_reduce_topk<DT><<<geo.emit_blocks, kThreads, 0, s>>>(rig, rays, fp, t, out);
+    if ((err = launch_k(pdl, k_reduce_topk<DT>, eb, th, 0, s, rig, rays, fp, t, out)) != cudaSuccess) return err;
   } else {
-    if (traced)
-      k_assign<DT, false, true><<<t.n_tiles, kAssignThreads, assign_smem(geo.tiles.k1), s>>>(
-          rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
-    else
-      k_assign<DT, false, false><<<t.n_tiles, kAssignThreads, assign_smem(geo.tiles.k1), s>>>(
-          rig, rays, fp, t, tr, (float)out.unit_m, geo.tiles);
+    const size_t sm = assign_smem(geo.tiles.k1);
+    err = traced ? launch_k(pdl, k_assign<DT, false, true>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles)
+                 : launch_k(pdl, k_assign<DT, false, false>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles);
+    if (err != cudaSuccess) return err;
     mark(3);
-    k_reduce<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+    if ((err = launch_k(pdl, k_reduce, eb, th, 0, s, t, out)) != cudaSuccess) return err;
   }
   mark(4);
-  k_scan<<<t.n_wblocks, 1024, 0, s>>>(t, out);
+  if ((err = launch_k(pdl, k_scan, dim3(t.n_wblocks), dim3(1024), 0, s, t, out)) != cudaSuccess) return err;
   mark(5);
-  k_emit<<<geo.emit_blocks, kThreads, 0, s>>>(t, out);
+  if ((err = launch_k(pdl, k_emit, eb, th, 0, s, t, out)) != cudaSuccess) return err;
   mark(6);
   return cudaGetLastError();
 }

@@ -81,11 +81,11 @@ class fuseflow_host_cloud(C.Structure):
 
 class fuseflow_tuning(C.Structure):
     _fields_ = [("count_chunks", C.c_int32), ("emit_blocks", C.c_int32),
-                ("prefetch_tiles", C.c_int32), ("reserved", C.c_int32)]
+                ("prefetch_tiles", C.c_int32), ("programmatic", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {"count_chunks": self.count_chunks, "emit_blocks": self.emit_blocks,
-                "prefetch_tiles": self.prefetch_tiles}
+                "prefetch_tiles": self.prefetch_tiles, "programmatic": self.programmatic}
 
 
 class fuseflow_completion(C.Structure):
@@ -374,9 +374,10 @@ def fuseflow_get_tuning(ctx) -> fuseflow_tuning:
     return tu
 
 
-def fuseflow_set_tuning(ctx, count_chunks: int, emit_blocks: int, prefetch_tiles: int) -> int:
+def fuseflow_set_tuning(ctx, count_chunks: int, emit_blocks: int, prefetch_tiles: int,
+                        programmatic: int = 0) -> int:
     """Status of replacing the context's launch geometry (INVALID_ARG leaves it unchanged)."""
-    tu = fuseflow_tuning(count_chunks, emit_blocks, prefetch_tiles, 0)
+    tu = fuseflow_tuning(count_chunks, emit_blocks, prefetch_tiles, programmatic)
     return load().fuseflow_set_tuning(ctx, C.byref(tu))
 
 
@@ -533,9 +534,10 @@ class FuseFlow:
     def tuning(self) -> dict:
         return fuseflow_get_tuning(self.ctx).as_dict()
 
-    def set_tuning(self, count_chunks: int, emit_blocks: int, prefetch_tiles: int):
-        _check(fuseflow_set_tuning(self.ctx, count_chunks, emit_blocks, prefetch_tiles),
-               "fuseflow_set_tuning")
+    def set_tuning(self, count_chunks: int, emit_blocks: int, prefetch_tiles: int,
+                   programmatic: int = 0):
+        _check(fuseflow_set_tuning(self.ctx, count_chunks, emit_blocks, prefetch_tiles,
+                                   programmatic), "fuseflow_set_tuning")
 
     def set_trace(self, **arrays):
         fuseflow_set_trace(self.ctx, **{k: (v.data_ptr() if v is not None else 0)

@@ -11,8 +11,9 @@ from parity import run_gpu
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# (count_chunks, emit_blocks, prefetch_tiles): the extremes of each range and a few between
-SETTINGS = [(1, 1, 0), (64, 65536, 1), (2, 152, 304), (7, 999, 1 << 20), (64, 3, 0)]
+# (count_chunks, emit_blocks, prefetch_tiles, programmatic): the extremes of each range and a
+# few between, programmatic launches on and off
+SETTINGS = [(1, 1, 0, 1), (64, 65536, 1, 0), (2, 152, 304, 1), (7, 999, 1 << 20, 0), (64, 3, 0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -60,9 +61,10 @@ def test_every_setting_gives_the_same_result(ffmod, case, top_k):
         trace = name != "8x1280x720"
         base = run_gpu(ff, fr, torch, with_trace=trace)
         assert base["stats"]["n_cells"] > 0
-        for cc, eb, pf in SETTINGS:
-            ff.set_tuning(cc, eb, pf)
-            assert ff.tuning() == {"count_chunks": cc, "emit_blocks": eb, "prefetch_tiles": pf}
+        for cc, eb, pf, pg in SETTINGS:
+            ff.set_tuning(cc, eb, pf, pg)
+            assert ff.tuning() == {"count_chunks": cc, "emit_blocks": eb, "prefetch_tiles": pf,
+                                   "programmatic": pg}
             _same(base, run_gpu(ff, fr, torch, with_trace=trace), with_trace=trace)
     finally:
         ff.close()
@@ -74,8 +76,9 @@ def test_out_of_range_settings_are_refused_without_effect(ffmod):
     try:
         before = ff.tuning()
         assert before["count_chunks"] >= 1 and before["emit_blocks"] >= 1
-        for cc, eb, pf in [(0, 8, 0), (65, 8, 0), (1, 0, 0), (1, 65537, 0), (1, 8, -1)]:
-            assert ffmod.fuseflow_set_tuning(ff.ctx, cc, eb, pf) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+        for cc, eb, pf, pg in [(0, 8, 0, 0), (65, 8, 0, 0), (1, 0, 0, 0), (1, 65537, 0, 0),
+                               (1, 8, -1, 0), (1, 8, 0, 2), (1, 8, 0, -1)]:
+            assert ffmod.fuseflow_set_tuning(ff.ctx, cc, eb, pf, pg) == ffmod.FUSEFLOW_ERR_INVALID_ARG
             assert ff.tuning() == before
     finally:
         ff.close()
@@ -100,6 +103,7 @@ def test_autotune_keeps_the_result_and_a_setting_no_slower(ffmod):
         assert 0 < us1 <= us0
         assert ff.tuning() == tu.as_dict()
         assert 1 <= tu.count_chunks <= 64 and tu.emit_blocks >= 1 and tu.prefetch_tiles >= 0
+        assert tu.programmatic in (0, 1)
         _same(base, run_gpu(ff, fr, torch, with_trace=False), with_trace=False)
     finally:
         ff.close()
