@@ -253,19 +253,20 @@ const char *fuseflow_stage_name(int stage);
  *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
  *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
  *                   depth rows into L2; 0 turns the prefetch off
- *   programmatic    1: each kernel of a frame after the first is launched with
+ *   programmatic    2: each kernel of a frame after the first is launched with
  *                   programmatic stream serialization, so that its blocks start while the
  *                   previous kernel's last blocks finish (they wait for its results on the
- *                   device); 0: plain stream order.  Stage timing always uses plain order.
+ *                   device); 1: the same except between the assign and reduce steps (early
+ *                   reduce blocks slow the assign step's last wave on large frames); 0:
+ *                   plain stream order.  Stage timing always uses plain order.
  * fuseflow_create picks count_chunks for one wave of four count blocks per SM (at most 6),
  * emit_blocks = 8 blocks per SM, prefetch_tiles = one wave of assign blocks, and
- * programmatic = 1 for rigs of fewer than 2^21 pixels (where the kernel boundaries are a
- * large share of the frame), 0 otherwise. */
+ * programmatic = 2 for rigs of fewer than 2^21 pixels, 1 otherwise. */
 typedef struct fuseflow_tuning {
   int32_t count_chunks;
   int32_t emit_blocks;
   int32_t prefetch_tiles;
-  int32_t programmatic;       /* 0 or 1 */
+  int32_t programmatic;       /* 0, 1 or 2 */
 } fuseflow_tuning;
 
 /* Reads (get) or replaces (set) the context's launch geometry.  set returns INVALID_ARG,

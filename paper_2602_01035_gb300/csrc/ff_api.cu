@@ -376,7 +376,7 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
     ctx->geo.count_blocks_x = (int)((ctx->max_chunks + ctx->geo.count_chunks - 1) / ctx->geo.count_chunks);
   }
   ctx->geo.emit_blocks = std::max(1, sms * 8);
-  ctx->geo.pdl = off < (1ll << 21) ? 1 : 0;
+  ctx->geo.pdl = off < (1ll << 21) ? 2 : 1;
 
   // ---------------------------------------------------------------- device memory
   int status = FUSEFLOW_OK;
@@ -900,9 +900,9 @@ struct Autotuner {
       c.prefetch_tiles = a;
       if ((st = consider(c)) != FUSEFLOW_OK) return st;
     }
-    {
+    for (int pg : {0, 1, 2}) {
       fuseflow_tuning c = best;
-      c.programmatic = 1 - best.programmatic;
+      c.programmatic = pg;
       if ((st = consider(c)) != FUSEFLOW_OK) return st;
     }
     // both settings timed again back to back, so that clocks drift into neither
@@ -927,7 +927,7 @@ int fuseflow_get_tuning(const fuseflow_ctx* ctx, fuseflow_tuning* out) {
 
 int fuseflow_set_tuning(fuseflow_ctx* ctx, const fuseflow_tuning* in) {
   if (!ctx || !in || in->count_chunks < 1 || in->count_chunks > 64 || in->emit_blocks < 1 ||
-      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || (in->programmatic != 0 && in->programmatic != 1))
+      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || in->programmatic < 0 || in->programmatic > 2)
     return FUSEFLOW_ERR_INVALID_ARG;
   apply_tuning(ctx, *in);
   return FUSEFLOW_OK;
@@ -1163,7 +1163,7 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   geo.emit_blocks = std::max(1, sms * 8);
-  geo.pdl = 1;                                         // at most 2^19 pixels: small frames
+  geo.pdl = 2;                                         // at most 2^19 pixels: small frames
   Tables t = static_tables(base, n_px, geo.count_blocks_x * n_cams);
   t.n_min = params->n_min;
   t.max_level = params->max_level;

@@ -88,7 +88,7 @@ struct Geometry {
   int count_chunks;              // 2048-pixel chunks per block of the coarse-count step
   int emit_blocks;
   int top_k;                     // Sec. II.5(2)a variant (0: every member is fused)
-  int pdl;                       // programmatic launches between the frame's kernels
+  int pdl;                       // programmatic launches: 0 none, 1 all but assign -> reduce, 2 all
   TileIndex tiles;               // assign-step tiles
 };
 

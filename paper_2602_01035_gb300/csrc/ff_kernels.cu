@@ -1845,9 +1845,11 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
     if ((err = launch_screen(a, sizeof(DT) == 4, geo.max_px, s)) != cudaSuccess) return err;
   }
   mark(1);
-  // programmatic launches between the frame's kernels when the geometry asks for them,
-  // never while stage events are recorded between them
-  const bool pdl = geo.pdl && ev == nullptr;
+  // programmatic launches between the frame's kernels when the geometry asks for them
+  // (level 2 also between the assign and reduce steps), never while stage events are
+  // recorded between them
+  const bool pdl = geo.pdl >= 1 && ev == nullptr;
+  const bool pdl_reduce = geo.pdl >= 2 && ev == nullptr;
   const float um = (float)out.unit_m;
   if ((err = launch_k(false, k_count<DT>, dim3(geo.count_blocks_x, geo.n_cams), dim3(kThreads), 0, s, rig, rays,
                       fp, t, geo.count_blocks_x, geo.count_chunks)) != cudaSuccess ||
@@ -1863,14 +1865,15 @@ cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs&
                             geo.tiles);
     if (err != cudaSuccess) return err;
     mark(3);
-    if ((err = launch_k(pdl, k_reduce_topk<DT>, eb, th, 0, s, rig, rays, fp, t, out)) != cudaSuccess) return err;
+    if ((err = launch_k(pdl_reduce, k_reduce_topk<DT>, eb, th, 0, s, rig, rays, fp, t, out)) != cudaSuccess)
+      return err;
   } else {
     const size_t sm = assign_smem(geo.tiles.k1);
     err = traced ? launch_k(pdl, k_assign<DT, false, true>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles)
                  : launch_k(pdl, k_assign<DT, false, false>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles);
     if (err != cudaSuccess) return err;
     mark(3);
-    if ((err = launch_k(pdl, k_reduce, eb, th, 0, s, t, out)) != cudaSuccess) return err;
+    if ((err = launch_k(pdl_reduce, k_reduce, eb, th, 0, s, t, out)) != cudaSuccess) return err;
   }
   mark(4);
   if ((err = launch_k(pdl, k_scan, dim3(t.n_wblocks), dim3(1024), 0, s, t, out)) != cudaSuccess) return err;

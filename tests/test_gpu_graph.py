@@ -75,7 +75,7 @@ def test_replay_keeps_its_geometry_and_trace(ffmod):
         nview = torch.full((npx,), -7, dtype=torch.int32, device=dev)
         key = torch.zeros((npx,), dtype=torch.int64, device=dev)
         ff.set_trace(nview=nview, key=key)
-        ff.set_tuning(1, 1, 0, 1)
+        ff.set_tuning(1, 1, 0, 2)
         graph = ff.graph(*bufs)
         ff.clear_trace()
         ff.set_tuning(64, 4096, 1, 0)       # later changes do not reach the recorded call

@@ -134,7 +134,7 @@ def test_overflowing_tiles_are_bitwise_reproducible(ffmod, oracle_mod):
         ff = ffmod.FuseFlow(rig, **params)
         try:
             if trial == 1:
-                ff.set_tuning(1, 1, 0, 1 - ff.tuning()["programmatic"])
+                ff.set_tuning(1, 1, 0, 2 - ff.tuning()["programmatic"])
             for _ in range(3):
                 o = run_gpu(ff, fr, torch, with_trace=True)
                 assert o["stats"] == ref["stats"]

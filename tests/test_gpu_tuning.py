@@ -12,8 +12,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # (count_chunks, emit_blocks, prefetch_tiles, programmatic): the extremes of each range and a
-# few between, programmatic launches on and off
-SETTINGS = [(1, 1, 0, 1), (64, 65536, 1, 0), (2, 152, 304, 1), (7, 999, 1 << 20, 0), (64, 3, 0, 1)]
+# few between, every level of programmatic launch
+SETTINGS = [(1, 1, 0, 2), (64, 65536, 1, 0), (2, 152, 304, 1), (7, 999, 1 << 20, 2), (64, 3, 0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -77,7 +77,7 @@ def test_out_of_range_settings_are_refused_without_effect(ffmod):
         before = ff.tuning()
         assert before["count_chunks"] >= 1 and before["emit_blocks"] >= 1
         for cc, eb, pf, pg in [(0, 8, 0, 0), (65, 8, 0, 0), (1, 0, 0, 0), (1, 65537, 0, 0),
-                               (1, 8, -1, 0), (1, 8, 0, 2), (1, 8, 0, -1)]:
+                               (1, 8, -1, 0), (1, 8, 0, 3), (1, 8, 0, -1)]:
             assert ffmod.fuseflow_set_tuning(ff.ctx, cc, eb, pf, pg) == ffmod.FUSEFLOW_ERR_INVALID_ARG
             assert ff.tuning() == before
     finally:
@@ -103,7 +103,7 @@ def test_autotune_keeps_the_result_and_a_setting_no_slower(ffmod):
         assert 0 < us1 <= us0
         assert ff.tuning() == tu.as_dict()
         assert 1 <= tu.count_chunks <= 64 and tu.emit_blocks >= 1 and tu.prefetch_tiles >= 0
-        assert tu.programmatic in (0, 1)
+        assert tu.programmatic in (0, 1, 2)
         _same(base, run_gpu(ff, fr, torch, with_trace=False), with_trace=False)
     finally:
         ff.close()
