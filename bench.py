@@ -307,7 +307,12 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     if args.slots > 1:
         B = args.slots
+        # several frames in flight: plain stream order (the streams fill the kernel
+        # boundaries; programmatic launches measured slower here)
         ctxs = [ff] + [tuned(F.FuseFlow(rig)) for _ in range(B - 1)]
+        g_ = tuning["chosen"]
+        for c_ in ctxs:
+            c_.set_tuning(g_["count_chunks"], g_["emit_blocks"], g_["prefetch_tiles"], 0)
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(B - 1)]
 
         def batched_step():
@@ -346,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
                            f"CUDA events around the step"}
         for c in ctxs[1:]:
             c.close()
+        tuned(ff)                               # the chosen setting again for the lines below
 
     # ------------------------------------------------------------ Sec. II.5(2)a top-3 variant
     # (consistency and weights for each cell's 3 most confident members only): same frames,

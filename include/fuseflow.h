@@ -375,6 +375,9 @@ typedef struct {
 int fuseflow_server_create(int64_t hbm_budget_bytes, fuseflow_server **out);
 
 /* Adds a rig (as fuseflow_create) with n_slots >= 1 frame slots; *rig_id receives its id.
+ * With several slots the frames of the rig run with programmatic = 0 (fuseflow_tuning):
+ * the slots' overlapping streams fill the kernel boundaries, and blocks waiting for an
+ * earlier kernel would only hold back the other slots' work.
  * Returns CAPACITY, with nothing allocated, if the slots would exceed the budget. */
 int fuseflow_server_add_rig(fuseflow_server *srv, const fuseflow_intrinsics *intr,
                             const fuseflow_extrinsics *extr, int32_t n_cams,
@@ -398,7 +401,8 @@ int64_t fuseflow_server_pending(const fuseflow_server *srv);
 
 /* Autotunes the launch geometry of rig `rig` (fuseflow_autotune on the context of its
  * first slot, with one sample frame given as HOST pointers as for submit) and applies the
- * chosen setting to all of the rig's slots.  The rig must be idle: INVALID_ARG while any
+ * chosen setting to all of the rig's slots (programmatic = 0 with several slots, as in
+ * fuseflow_server_add_rig).  The rig must be idle: INVALID_ARG while any
  * of its frames is in flight or waiting.  Synchronous.  *chosen and frame_us as for
  * fuseflow_autotune (either may be NULL). */
 int fuseflow_server_autotune(fuseflow_server *srv, int32_t rig, const void *const *depth,

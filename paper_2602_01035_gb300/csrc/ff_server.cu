@@ -220,6 +220,12 @@ int fuseflow_server_add_rig(fuseflow_server* srv, const fuseflow_intrinsics* int
       st = FUSEFLOW_ERR_CUDA;
       break;
     }
+    if (n_slots > 1) {                     // overlapping slots fill the kernel boundaries
+      fuseflow_tuning tu{};
+      fuseflow_get_tuning(s.ctx, &tu);
+      tu.programmatic = 0;
+      fuseflow_set_tuning(s.ctx, &tu);
+    }
     if ((st = record(g, s)) != FUSEFLOW_OK) {
       release_slot(s);
       break;
@@ -318,6 +324,7 @@ int fuseflow_server_autotune(fuseflow_server* srv, int32_t rig, const void* cons
   st = fuseflow_autotune(s.ctx, in.depth.data(), in.conf.data(), in.rgb.data(), reps, &tu, frame_us,
                          s.stream);
   if (st != FUSEFLOW_OK) return st;
+  if (g.slots.size() > 1) tu.programmatic = 0;   // see fuseflow_server_add_rig
   for (Slot& o : g.slots) {
     fuseflow_set_tuning(o.ctx, &tu);
     if ((st = record(g, o)) != FUSEFLOW_OK) return st;
