@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson arrival trace of the served/plain comparison")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-max-inflight", type=int, default=0,
+                    help="frames on the device at once in the served replay (0: every free slot)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep fuseflow_create's launch geometry instead of the autotuner's")
     return ap.parse_args()
@@ -576,9 +578,23 @@ def run_ours(args, rank, world, local_rank):
         configs = run_configs(dev)
 
     # ------------------------------------------------------------ served vs plain
+    # in a fresh process on the same GPU (this one stays idle meanwhile): the latency tail of
+    # a wall-clock replay measured inside this long-running process came out 15-30 times
+    # longer, for the served and the plain path alike, than in a process of its own
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
-        serving = run_serving(args, dev)
+        import multiprocessing as mp
+        import queue as _queue
+        torch.cuda.synchronize(dev)
+        ctx_ = mp.get_context("spawn")
+        q_ = ctx_.Queue()
+        child = ctx_.Process(target=serving_child, args=(vars(args), local_rank, q_))
+        child.start()                    # not a pool worker: it renders with a pool itself
+        try:
+            serving = q_.get(timeout=3600)
+        except _queue.Empty:
+            serving = {"error": "the serving replay process returned nothing"}
+        child.join()
 
     # ------------------------------------------------------------ CPU baseline (oracle)
     cpu = None
@@ -746,6 +762,17 @@ def run_ablations(dev, rig, frames, frames_each: int = 64):
 SERVE_BUDGET = 40 << 30          # HBM budget of the served rigs' slots (bytes)
 
 
+def serving_child(arg_dict, local_rank, out_queue):
+    """run_serving in a process of its own (module level, for a spawn context)."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    try:
+        res = run_serving(argparse.Namespace(**arg_dict), torch.device("cuda", local_rank))
+    except Exception as exc:                     # reported in the JSON line, not raised
+        res = {"error": f"{type(exc).__name__}: {exc}"}
+    out_queue.put(res)
+
+
 def run_serving(args, dev):
     """Served vs plain on one seeded Poisson trace over 12 rigs of 2-24 cameras at
     320x240 to 1920x1080 (15-60 fps per rig), frames from pinned host memory."""
@@ -778,6 +805,7 @@ def run_serving(args, dev):
             except F.FuseFlowError:
                 if k == 1:
                     raise
+    srv.set_max_inflight(args.serve_max_inflight)
     from collections import deque
     outs = [deque(SV.HostCloud(caps[r]) for _ in range(slots[r] + 1)) for r in range(n)]
     # warm-up: one frame per rig
@@ -809,7 +837,8 @@ def run_serving(args, dev):
                     f"15-60 fps per rig for {args.serve_seconds:g} s ({len(trace)} frames, "
                     f"{sum(px) / 1e6:.1f} Mpx per round of all rigs); frames from pinned host memory, "
                     f"results into pinned host arrays; one rendered frame per rig, resubmitted",
-        "served": dict(served, slots_per_rig=slots, hbm_bytes=int(srv_bytes), budget=SERVE_BUDGET),
+        "served": dict(served, slots_per_rig=slots, hbm_bytes=int(srv_bytes), budget=SERVE_BUDGET,
+                       max_inflight=args.serve_max_inflight),
         "plain": dict(plain, path="one fuseflow_fuse_frame_host call at a time, arrival order"),
         "saturated": {"served_frames_per_s": served_sat["frames_per_s"],
                       "plain_frames_per_s": plain_sat["frames_per_s"],

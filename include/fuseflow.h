@@ -342,8 +342,9 @@ int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_e
  * rig gets n_slots frame slots, each with its own device tables, input staging buffers
  * and stream; the slots of all rigs are allocated up front against an HBM budget.  A
  * submitted frame starts at once when one of its rig's slots is free, otherwise it waits
- * in the rig's FIFO and starts as soon as fuseflow_server_poll finds a slot finished, so
- * the copies and kernels of frames of different rigs and slots overlap on the device.
+ * and starts as soon as fuseflow_server_poll finds a slot of its rig finished (among the
+ * waiting frames whose rig has a free slot, the one submitted first starts first), so the
+ * copies and kernels of frames of different rigs and slots overlap on the device.
  * Results do not depend on the mix: every frame runs the same kernels on its own tables.
  * Not thread-safe: drive one server from one host thread.
  * ------------------------------------------------------------------------------------ */
@@ -395,6 +396,13 @@ int fuseflow_server_submit(fuseflow_server *srv, int32_t rig, const void *const 
  * their number in *n_done, and starts waiting frames on the slots that became free. */
 int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_t max_done,
                          int32_t *n_done);
+
+/* Caps the frames on the device at once over all rigs (0, the default: every free slot
+ * takes a frame).  Waiting frames start in submission order across rigs, each as soon as
+ * a slot of its rig is free and the cap allows; a lower cap gives each frame more of the
+ * GPU and shortens the latency tail when many frames arrive together, at some loss of
+ * overlap.  Returns INVALID_ARG for a negative cap, else as fuseflow_server_poll. */
+int fuseflow_server_set_max_inflight(fuseflow_server *srv, int32_t max_inflight);
 
 /* Frames submitted but not yet reported by fuseflow_server_poll. */
 int64_t fuseflow_server_pending(const fuseflow_server *srv);

@@ -63,6 +63,8 @@ struct fuseflow_server {
   int64_t used = 0;
   int64_t next_id = 1;
   int64_t pending = 0;
+  int32_t max_inflight = 0;             // frames on the device at once, 0 = every free slot
+  int32_t inflight = 0;
   std::vector<Rig> rigs;
 };
 
@@ -157,6 +159,37 @@ int start(Rig& g, Slot& s, const Request& r) {
   s.request = r.id;
   s.capacity = r.out.capacity;
   return FUSEFLOW_OK;
+}
+
+// Starts waiting frames while the cap allows: each time the oldest waiting frame (lowest
+// request id, i.e. submission order across rigs) among the rigs with a free slot.
+// Returns the first error of a start that failed (the frame is dropped).
+int fill_slots(fuseflow_server* srv) {
+  int status = FUSEFLOW_OK;
+  while (srv->max_inflight == 0 || srv->inflight < srv->max_inflight) {
+    Rig* best = nullptr;
+    Slot* free_slot = nullptr;
+    for (Rig& g : srv->rigs) {
+      if (g.waiting.empty() || (best && g.waiting.front().id > best->waiting.front().id)) continue;
+      for (Slot& sl : g.slots)
+        if (!sl.busy) {
+          best = &g;
+          free_slot = &sl;
+          break;
+        }
+    }
+    if (!best) break;
+    Request r = std::move(best->waiting.front());
+    best->waiting.pop_front();
+    const int st = start(*best, *free_slot, r);
+    if (st == FUSEFLOW_OK) {
+      ++srv->inflight;
+    } else {
+      if (status == FUSEFLOW_OK) status = st;
+      --srv->pending;                      // dropped: reported through the return value
+    }
+  }
+  return status;
 }
 
 int status_of(const fuseflow_stats& st, int64_t capacity) {
@@ -260,15 +293,17 @@ int fuseflow_server_submit(fuseflow_server* srv, int32_t rig, const void* const*
   }
   r.out = *out;
   *request = r.id;
-  for (Slot& s : g.slots) {
-    if (s.busy) continue;
-    const int st = start(g, s, r);
-    if (st == FUSEFLOW_OK) ++srv->pending;
-    return st;
-  }
+  // the frame queues behind every frame submitted before it and starts at once if a slot
+  // of its rig is free and the cap allows
   g.waiting.push_back(std::move(r));
   ++srv->pending;
-  return FUSEFLOW_OK;
+  return fill_slots(srv);
+}
+
+int fuseflow_server_set_max_inflight(fuseflow_server* srv, int32_t max_inflight) {
+  if (!srv || max_inflight < 0) return FUSEFLOW_ERR_INVALID_ARG;
+  srv->max_inflight = max_inflight;
+  return fill_slots(srv);
 }
 
 int fuseflow_server_poll(fuseflow_server* srv, fuseflow_completion* done, int32_t max_done,
@@ -290,19 +325,12 @@ int fuseflow_server_poll(fuseflow_server* srv, fuseflow_completion* done, int32_
       if (q != cudaSuccess) cudaGetLastError();
       s.busy = false;
       --srv->pending;
-      // continuous batching: the slot takes the rig's oldest waiting frame at once
-      if (!g.waiting.empty()) {
-        Request r = std::move(g.waiting.front());
-        g.waiting.pop_front();
-        const int st = start(g, s, r);
-        if (st != FUSEFLOW_OK) {
-          status = st;
-          --srv->pending;                  // dropped: reported through the return value
-        }
-      }
+      --srv->inflight;
     }
   }
-  return status;
+  // continuous batching: freed slots take the oldest waiting frames at once
+  const int st = fill_slots(srv);
+  return status != FUSEFLOW_OK ? status : st;
 }
 
 int fuseflow_server_autotune(fuseflow_server* srv, int32_t rig, const void* const* depth,

@@ -151,6 +151,7 @@ EXPORTS = {
                                          C.POINTER(fuseflow_host_cloud), C.POINTER(C.c_int64)]),
     "fuseflow_server_poll": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_completion), C.c_int32,
                                        C.POINTER(C.c_int32)]),
+    "fuseflow_server_set_max_inflight": (C.c_int, [C.c_void_p, C.c_int32]),
     "fuseflow_server_pending": (C.c_int64, [C.c_void_p]),
     "fuseflow_server_device_bytes": (C.c_int64, [C.c_void_p]),
     "fuseflow_server_destroy": (None, [C.c_void_p]),
@@ -431,6 +432,11 @@ def fuseflow_server_poll(srv, buf, max_done: int):
     n = C.c_int32()
     _check(load().fuseflow_server_poll(srv, buf, max_done, C.byref(n)), "fuseflow_server_poll")
     return n.value
+
+
+def fuseflow_server_set_max_inflight(srv, max_inflight: int) -> None:
+    _check(load().fuseflow_server_set_max_inflight(srv, max_inflight),
+           "fuseflow_server_set_max_inflight")
 
 
 def fuseflow_server_pending(srv) -> int:

@@ -10,8 +10,10 @@ time from a frame's arrival to the host seeing its result.  All fusion work runs
 from __future__ import annotations
 
 import ctypes as C
+import gc
 import time
 from collections import deque
+from contextlib import contextmanager
 
 import numpy as np
 
@@ -102,6 +104,10 @@ class Server:
         return [(self._done[i].request, self._done[i].rig, self._done[i].status,
                  self._done[i].stats.as_dict()) for i in range(n)]
 
+    def set_max_inflight(self, n: int) -> None:
+        """At most n frames on the device at once (0: every free slot)."""
+        F.fuseflow_server_set_max_inflight(self.srv, n)
+
     def pending(self) -> int:
         return F.fuseflow_server_pending(self.srv)
 
@@ -126,6 +132,21 @@ class Server:
             pass
 
 
+@contextmanager
+def _no_gc_pauses():
+    """The cyclic garbage collector stays off while a trace is replayed: a full collection
+    of a large process can stall the polling loop for tens of milliseconds, which would show
+    up as frame latency (reference counting still frees everything the loop allocates)."""
+    gc.collect()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
 def _summary(lat_s, first_arrival, last_done, n, px_total, statuses):
     lat = np.sort(np.asarray(lat_s)) * 1e3
     span = max(last_done - first_arrival, 1e-9)
@@ -139,6 +160,11 @@ def _summary(lat_s, first_arrival, last_done, n, px_total, statuses):
 def replay_served(server: Server, rig_ids, frames, outputs, trace, px_per_rig):
     """Replays `trace` in wall-clock time through the server.  frames[r] is rig r's pinned
     frame, outputs[r] a deque of HostCloud buffers (at least one per slot)."""
+    with _no_gc_pauses():
+        return _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig)
+
+
+def _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig):
     t0 = time.perf_counter()
     nxt, inflight, lat, statuses, px = 0, {}, [], [], 0
     last = t0
@@ -173,6 +199,11 @@ def replay_served(server: Server, rig_ids, frames, outputs, trace, px_per_rig):
 def replay_plain(contexts, frames, outputs, trace, px_per_rig, stream: int = 0):
     """The same trace through the plain path: one synchronous fuse_frame_host per frame,
     in arrival order (a frame waits for every earlier one)."""
+    with _no_gc_pauses():
+        return _replay_plain(contexts, frames, outputs, trace, px_per_rig, stream)
+
+
+def _replay_plain(contexts, frames, outputs, trace, px_per_rig, stream):
     t0 = time.perf_counter()
     lat, statuses, px = [], [], 0
     first = trace[0][0] if trace else 0.0

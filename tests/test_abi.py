@@ -199,3 +199,8 @@ def test_struct_layouts_match_the_header(ffmod, tmp_path):
         assert int(got[name]) == C.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"
+
+
+def test_server_cap_rejects_bad_arguments_without_a_gpu(ffmod):
+    lib = ffmod.load()
+    assert lib.fuseflow_server_set_max_inflight(None, 2) == ffmod.FUSEFLOW_ERR_INVALID_ARG

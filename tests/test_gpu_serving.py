@@ -159,3 +159,29 @@ def test_top_k_and_screened_rigs_serve_the_same_results(mods):
     finally:
         srv.close()
 
+
+
+def test_in_flight_cap_starts_frames_in_submission_order(mods):
+    F, SV = mods
+    cases = _cases()
+    alone = [_alone(F, r, f) for r, f in cases]
+    srv = SV.Server(8 << 30)
+    try:
+        rids = [srv.add_rig(r, n_slots=2) for r, _ in cases]
+        srv.set_max_inflight(1)                  # one frame at a time: strict FIFO over rigs
+        frames = [SV.pinned_frame(f) for _, f in cases]
+        order = [2, 0, 1, 1, 2, 0]
+        bufs = {}
+        for r in order:
+            hc = SV.HostCloud(srv.rigs[r]["capacity"])
+            bufs[srv.submit(rids[r], frames[r], hc)] = (r, hc)
+        done = srv.drain()
+        assert [d[0] for d in done] == sorted(bufs)
+        for req, rig, status, st in done:
+            r, hc = bufs[req]
+            assert status == F.FUSEFLOW_OK and rig == rids[r]
+            _same(hc.cells(st["n_cells"]), alone[r]["cells"])
+        with pytest.raises(F.FuseFlowError):
+            srv.set_max_inflight(-1)
+    finally:
+        srv.close()
