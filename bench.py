@@ -763,7 +763,11 @@ SERVE_BUDGET = 40 << 30          # HBM budget of the served rigs' slots (bytes)
 
 
 def serving_child(arg_dict, local_rank, out_queue):
-    """run_serving in a process of its own (module level, for a spawn context)."""
+    """run_serving in a process of its own (module level, for a spawn context).  The server
+    gives each of its 24 slots a stream; with CUDA's default 8 hardware work queues, streams
+    that share a queue serialise, which lengthened the latency tail, so this process asks
+    for 32 before it initialises CUDA."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     torch.cuda.set_device(local_rank)
     try:

@@ -346,6 +346,9 @@ int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_e
  * waiting frames whose rig has a free slot, the one submitted first starts first), so the
  * copies and kernels of frames of different rigs and slots overlap on the device.
  * Results do not depend on the mix: every frame runs the same kernels on its own tables.
+ * Each slot has a stream of its own: with many slots, set CUDA_DEVICE_MAX_CONNECTIONS=32
+ * in the environment before the process initialises CUDA, since streams that share one
+ * of the default 8 hardware work queues run one after the other.
  * Not thread-safe: drive one server from one host thread.
  * ------------------------------------------------------------------------------------ */
 typedef struct fuseflow_server fuseflow_server;
