@@ -1,7 +1,9 @@
 // ff_kernels.cu - sm_103a kernels of the FUSE-Flow per-frame fusion path.
 //
-// Launch sequence of one frame (all on the caller's stream):
+// Launch sequence of one frame (all on the caller's stream; from the level step on,
+// optionally as programmatic dependent launches, see pdl_release / pdl_wait):
 //   memset   frame counters + representative bitmap
+//   screen   (only with a depth screen set) D^r of Eq. 8 into the context's buffers
 //   count    (a) decode + gate + back-project (Eq. 8, 9), coarse density n_c (Sec. II.5(1)c)
 //            from equal-cell runs merged across each warp, per-block pixel counts and
 //            extent (Sec. II.5(1)b)
@@ -14,10 +16,13 @@
 //            (Eq. 11), written as one partial record pushed onto its cell's list
 //   reduce   per cell: walk its partials, combine them, stage the fused cell, mark its
 //            representative; the used slots and coarse entries are cleared for the next frame
+//            (top-k variant: k_reduce_topk weighs and fuses each cell's k most confident
+//            members here instead)
 //   scan     ranks of the representatives (output order) and frame statistics
 //   emit     fused cells in representative order
-// Outside the frame sequence: k_copyout (served frames: cloud into pinned host memory)
-// and k_mc (the multi-camera depth consistency error of Eq. 12 on a point set).
+// Outside the frame sequence: k_copyout (served frames: cloud into pinned host memory),
+// k_mc (the multi-camera depth consistency error of Eq. 12 on a point set), k_confidence
+// (Eq. 3 confidence from depth) and the stand-alone depth screen.
 //
 // Every reduction of the frame is order-independent (integer counts, max, min and
 // fixed-point sums), so its output is bitwise reproducible.
