@@ -388,15 +388,19 @@ int fuseflow_server_add_rig(fuseflow_server *srv, const fuseflow_intrinsics *int
                             const fuseflow_params *params, int32_t n_slots, int32_t *rig_id);
 
 /* Submits one frame of rig `rig`: depth[i], conf[i], rgb[i] are HOST pointers (pinned
- * for asynchronous copies) and *out the host output arrays; all stay valid and untouched
- * until the frame is reported complete.  Never blocks on the device.  *request receives
- * the frame's id.  Returns INVALID_ARG, CUDA. */
+ * for asynchronous copies) and *out the host output arrays (pinned: the copy-out kernel
+ * writes them through their mapped addresses); all stay valid and untouched until the
+ * frame is reported complete.  Never blocks on the device.  *request receives the frame's
+ * id.  Returns INVALID_ARG, or the status of a frame start that failed (as for
+ * fuseflow_server_poll; that frame may be this one or an earlier waiting one). */
 int fuseflow_server_submit(fuseflow_server *srv, int32_t rig, const void *const *depth,
                            const float *const *conf, const uint8_t *const *rgb,
                            const fuseflow_host_cloud *out, int64_t *request);
 
 /* Non-blocking: reports up to max_done finished frames (in completion order) in done[],
- * their number in *n_done, and starts waiting frames on the slots that became free. */
+ * their number in *n_done, and starts waiting frames on the slots that became free.  A
+ * waiting frame whose start fails (a CUDA error, host arrays that are not pinned) is
+ * dropped without a completion, and the first such status is returned. */
 int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_t max_done,
                          int32_t *n_done);
 
