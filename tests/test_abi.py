@@ -204,3 +204,25 @@ def test_struct_layouts_match_the_header(ffmod, tmp_path):
 def test_server_cap_rejects_bad_arguments_without_a_gpu(ffmod):
     lib = ffmod.load()
     assert lib.fuseflow_server_set_max_inflight(None, 2) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+
+
+def test_binding_fails_loudly_without_the_library(ffmod, tmp_path):
+    """No fallback: with the library missing, loading raises instead of computing elsewhere."""
+    saved_lib, saved_path = ffmod._lib, ffmod._build.LIB
+    try:
+        ffmod._lib = None
+        ffmod._build.LIB = str(tmp_path / "missing" / "libfuseflow.so")
+        with pytest.raises(ImportError):
+            ffmod.load(build_if_missing=False)
+    finally:
+        ffmod._lib, ffmod._build.LIB = saved_lib, saved_path
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: nothing in the package may import or run it."""
+    pkg = os.path.join(ROOT, "paper_2602_01035_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            text = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), name
+            assert "liboracle" not in text, name
