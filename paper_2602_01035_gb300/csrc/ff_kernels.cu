@@ -374,6 +374,8 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
   __shared__ unsigned s_fill;                                    // keys in the block table
+  __shared__ unsigned short s_occ[TS];                           // occupied positions, packed
+  __shared__ unsigned s_nocc;
   __shared__ unsigned s_red[kThreads / 32][9];
   const RigDev& rig = *rigp;
   const int cam = blockIdx.y;
@@ -387,7 +389,7 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
   const long long c0 = (long long)blockIdx.x * chunks;          // first chunk of 2048 pixels
   const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
-  if (threadIdx.x == 0) s_fill = 0u;
+  if (threadIdx.x == 0) { s_fill = 0u; s_nocc = 0u; }
   __syncthreads();
 
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
@@ -540,10 +542,22 @@ k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FrameP
     }
     t.bstats[bid] = b;
   }
+  // the block table into the global one: the occupied positions are packed first, so that a
+  // thread sends at most a few of them and the global round trips of all of them overlap
+  // (walking the table in strides left up to eight dependent round trips per thread)
   for (int i = threadIdx.x; i < TS; i += kThreads) {
-    const unsigned long long key = s_key[i];
-    if (key == kKeyEmpty) continue;
-    const unsigned slot = coarse_insert(t, key);
+    const bool occ = s_key[i] != kKeyEmpty;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    unsigned base = 0u;
+    if (lane == 0 && m) base = atomicAdd(&s_nocc, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) s_occ[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)i;
+  }
+  __syncthreads();
+  const int n_occ = (int)s_nocc;
+  for (int j = threadIdx.x; j < n_occ; j += kThreads) {
+    const int i = s_occ[j];
+    const unsigned slot = coarse_insert(t, s_key[i]);
     if (slot != kSlotNone) atomicAdd(&t.coarse[slot].count, s_cnt[i]);
   }
 }
