@@ -17,3 +17,24 @@ def oracle_mod():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+_PARITY = []
+
+
+@pytest.fixture(scope="session")
+def parity_log():
+    """Collects parity reports (counts of compared and excluded points and cells); written
+    as JSON to $FUSEFLOW_PARITY_LOG at the end of the session when that is set."""
+    def log(name, report):
+        _PARITY.append({"case": name, **report})
+        print(name, report)
+    return log
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("FUSEFLOW_PARITY_LOG")
+    if path and _PARITY:
+        import json
+        with open(path, "w") as f:
+            json.dump(_PARITY, f, indent=1)

@@ -1,21 +1,20 @@
-"""Parity at the largest sizes, in the launch configuration of the benchmark: the 32 x 1024^2
-rig-scaling rig and the largest serving rig (14 x 1920x1080).  The FP64 oracle cannot fuse
-frames of 29-34 M pixels in a test, so the check has two parts:
+"""Parity at the largest sizes, in the launch configuration of the benchmark.
 
-* per pixel, on a sample of rows (every 48th): the oracle's Eq. 8-10 values of a pixel
-  depend only on that pixel and the other views' full depth maps, so the sampled rows are
-  compared exactly as in the full parity tests (gate, world point, valid views, exponent,
-  weight; half-pixel ties excluded);
-* on the whole frame, properties that hold at any size: every gated in-range point is in
-  exactly one cell (the cells' counts are the histogram of the points' keys), each cell's
-  representative is a member of largest confidence with the lowest index among equals, and
-  the output is ordered by representative.
+* Whole frames against the oracle, every pixel and every cell (the comparison of the other
+  parity tests): the 16 and 32 x 1024^2 rig-scaling rigs (16.8 and 33.5 M pixels) and every
+  one of the 12 serving rigs (up to 14 x 1920x1080, 29 M pixels).
+* A fast variant on the same two largest rigs: per pixel on a sample of rows (every 48th;
+  a pixel's Eq. 8-10 values depend only on that pixel and the other views' full depth
+  maps), and on the whole frame, properties that hold at any size: every gated in-range
+  point is in exactly one cell (the cells' counts are the histogram of the points' keys),
+  each cell's representative is a member of largest confidence with the lowest index among
+  equals, and the output is ordered by representative.
 """
 import numpy as np
 import pytest
 
 from paper_2602_01035_gb300 import scenes as S
-from parity import W_ABS, W_FLOOR, run_gpu
+from parity import W_ABS, W_FLOOR, compare, run_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -106,3 +105,35 @@ def test_full_size_rig(ffmod, oracle_mod, name):
     first[1:] = k[o][1:] != k[o][:-1]
     best = dict(zip(k[o][first].tolist(), g[o][first].tolist()))
     assert all(best[int(kk)] == int(r) for kk, r in zip(cells["key"], rep)), "representative differs"
+
+
+def _whole_frame(ffmod, oracle_mod, rig, fr, parity_log, name):
+    ff = ffmod.FuseFlow(rig)
+    try:
+        gpu = run_gpu(ff, fr, torch, with_trace=True)
+    finally:
+        ff.close()
+    assert gpu["status"] == ffmod.FUSEFLOW_OK, gpu["stats"]
+    orc = oracle_mod.fuse_frame(rig, fr, {}, cell_capacity=max(1 << 20, rig.n_pixels // 4))
+    rep = compare(gpu, orc)
+    rep["pixels"] = rig.n_pixels
+    parity_log(name, rep)
+    return rep
+
+
+@pytest.mark.parametrize("n_cams", [16, 32])
+def test_whole_frame_rig_scaling(ffmod, oracle_mod, parity_log, n_cams):
+    rig, _, fr = S.config4(n_cams=n_cams)
+    rep = _whole_frame(ffmod, oracle_mod, rig, fr, parity_log, f"cfg4_{n_cams}x1024x1024")
+    assert rep["n_cells_oracle"] > 100000
+    assert rep["excluded_fraction"] < 0.2
+
+
+def test_whole_frame_every_serving_rig(ffmod, oracle_mod, parity_log):
+    rigs, _ = S.serving_rigs(12, 5999)
+    for i, rig in enumerate(rigs):
+        c = rig.cameras[0]
+        rep = _whole_frame(ffmod, oracle_mod, rig, S.serving_frame(i), parity_log,
+                           f"serving_rig{i}_{rig.n_cams}x{c.width}x{c.height}")
+        assert rep["n_cells_oracle"] > 1000
+        assert rep["excluded_fraction"] < 0.2

@@ -37,9 +37,10 @@ def _fuse_and_compare(ffmod, oracle_mod, rig, fr, params=None, trace=True):
     return compare(gpu, orc, oracle_mod), gpu, orc
 
 
-def test_config1_float_depth(ffmod, oracle_mod):
+def test_config1_float_depth(ffmod, oracle_mod, parity_log):
     rig, _, fr = S.config1()
     rep, gpu, orc = _fuse_and_compare(ffmod, oracle_mod, rig, fr)
+    parity_log("cfg1_2x160x120", rep)
     assert rep["n_cells_matched"] > 150
     assert rep["n_points_compared"] > 10000
 
@@ -61,27 +62,30 @@ def test_tiny_and_ragged(ffmod, oracle_mod, n, w, h, fmt, k, zero, seed):
     _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"k_views": k, "n_min": 4})
 
 
-def test_config2_frames(ffmod, oracle_mod):
+def test_config2_frames(ffmod, oracle_mod, parity_log):
     for f in (0, 17):
         rig, _, fr = S.config2(frame=f)
         rep, _, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr)
+        parity_log(f"cfg2_4x640x480_frame{f}", rep)
         assert rep["n_cells_matched"] > 5000
 
 
-def test_config3_full_frame(ffmod, oracle_mod):
+def test_config3_full_frame(ffmod, oracle_mod, parity_log):
     """8 x 1280x720 uint16: the benchmark's rig and launch configuration."""
     rig, _, fr = S.config3(frame=0)
     rep, gpu, orc = _fuse_and_compare(ffmod, oracle_mod, rig, fr)
-    assert rep["n_cells_matched"] > 100000
+    parity_log("cfg3_8x1280x720_frame0", rep)
+    assert rep["n_cells_oracle"] > 150000 and rep["excluded_fraction"] < 0.2
     lv = (gpu["cells"]["key"] >> np.uint64(60)).astype(int)
     assert len(np.unique(lv)) >= 3          # the adaptive partition uses several levels
     print(rep)
 
 
 @pytest.mark.parametrize("n_cams", [2, 8])
-def test_config4_rigs(ffmod, oracle_mod, n_cams):
+def test_config4_rigs(ffmod, oracle_mod, parity_log, n_cams):
     rig, _, fr = S.config4(n_cams=n_cams)
     rep, _, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr)
+    parity_log(f"cfg4_{n_cams}x1024x1024", rep)
     assert rep["n_cells_matched"] > 1000
 
 
@@ -164,9 +168,10 @@ def test_top_k_variant_ragged(ffmod, oracle_mod, n, w, h, fmt, seed):
     _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"top_k": 3, "n_min": 4})
 
 
-def test_top_k_variant_benchmark_rig(ffmod, oracle_mod):
+def test_top_k_variant_benchmark_rig(ffmod, oracle_mod, parity_log):
     rig, _, fr = S.config3(frame=0)
     rep, _, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr, {"top_k": 3})
+    parity_log("cfg3_8x1280x720_frame0_top3", rep)
     assert rep["n_cells_matched"] > 100000
 
 
@@ -192,17 +197,36 @@ def test_invalid_float_depth_values(ffmod, oracle_mod):
     _fuse_and_compare(ffmod, oracle_mod, rig, S.Frame(d, fr.conf, fr.rgb))
 
 
+def _patch_frame(fr, y0=40, x0=60, h=12, w=12):
+    """The frame with every depth sample zeroed except one patch of camera 0."""
+    depth = []
+    for i, d in enumerate(fr.depth):
+        z = np.zeros_like(d)
+        if i == 0:
+            z[y0:y0 + h, x0:x0 + w] = d[y0:y0 + h, x0:x0 + w]
+        depth.append(z)
+    return S.Frame(depth, fr.conf, fr.rgb)
+
+
 def test_capacity_overflow_reports_and_recovers(ffmod, oracle_mod):
+    """A frame with more cells than max_cells reports CAPACITY; the same context then fuses
+    a frame that fits exactly as the oracle does (the overflowed frame left no state behind),
+    and a context with room fuses the large frame."""
     rig, _, fr = S.config1()
+    small = _patch_frame(fr)
     ff = ffmod.FuseFlow(rig, max_cells=50)
     try:
         gpu = run_gpu(ff, fr, torch, with_trace=False)
         assert gpu["status"] == ffmod.FUSEFLOW_ERR_CAPACITY
         assert gpu["stats"]["n_cells"] == 50
+        for _ in range(2):                    # twice: the recovered frame leaves none either
+            after = run_gpu(ff, small, torch, with_trace=True)
+            assert after["status"] == ffmod.FUSEFLOW_OK, after["stats"]
+            rep = compare(after, oracle_mod.fuse_frame(rig, small, {}), oracle_mod)
+            assert 0 < rep["n_cells_oracle"] <= 50
+            assert rep["n_cells_matched"] + rep["n_cells_excluded"] == rep["n_cells_oracle"]
     finally:
         ff.close()
-    # a context with room fuses the same frame correctly afterwards, and the overflowed
-    # context's tables were cleaned (its next small frame is exact)
     rep, _, _ = _fuse_and_compare(ffmod, oracle_mod, rig, fr)
     assert rep["n_cells_matched"] > 150
 
