@@ -312,7 +312,7 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
  * Limits: at most 524,288 pixels per frame over all cameras, at most 65,536 ray-table
  * entries (sum over cameras of width + height), 2 (K - 1) times that at most 393,216
  * (K = min(k_views, n_cams)), and max_cells <= 32,768 (0 selects 32,768); larger
- * requests return FUSEFLOW_ERR_CAPACITY without touching the GPU.  A
+ * requests return FUSEFLOW_ERR_CAPACITY before anything is sent to the GPU.  A
  * frame that produces more than 131,072 (tile, cell) partial records reports a capacity
  * error in stats->error.
  * Inputs are device pointers as for fuseflow_fuse_frame; pos[3*max_cells],
@@ -324,9 +324,12 @@ int64_t fuseflow_device_bytes(const fuseflow_ctx *ctx);
  * The first call on each device looks the array's device address up with
  * cudaGetSymbolAddress, empties its hash tables and synchronizes `stream`; make that
  * first call before any stream capture.  Every later call reuses the array as the last
- * call left it (each frame empties the tables it used again).  Calls whose GPU work
- * overlaps, on several streams or from several host threads, race on the array: keep
- * them ordered on one stream. */
+ * call left it (each frame empties the tables it used again, also after a frame that
+ * reported a capacity error).  Calls whose GPU work overlaps, on several streams or from
+ * several host threads, race on the array: keep them ordered on one stream.  The call
+ * stages the rig constants through host arrays that the next call overwrites, so it must
+ * not be recorded into a CUDA graph: on a capturing stream it returns
+ * FUSEFLOW_ERR_INVALID_ARG and does nothing. */
 int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_extrinsics *extr,
                                int32_t n_cams, const fuseflow_params *params,
                                const void *const *depth, const float *const *conf,

@@ -1114,9 +1114,17 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
     if (!depth[i] || !conf[i] || !rgb[i]) return FUSEFLOW_ERR_INVALID_ARG;
   }
   const long long max_cells = params->max_cells > 0 ? params->max_cells : kStaticMaxCells;
-  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells)
+  const int K = std::min<int>(params->k_views, n_cams);
+  const int k1 = K - 1;
+  if (n_px > kStaticMaxPixels || n_rays > kStaticMaxRays || max_cells > kStaticMaxCells ||
+      2ll * k1 * n_rays > kStaticMaxPairRays)
     return FUSEFLOW_ERR_CAPACITY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the rig constants go through host staging arrays that the next call overwrites, so a
+  // captured call would replay another call's constants: capture is refused
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return FUSEFLOW_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FUSEFLOW_ERR_CUDA;
 
@@ -1127,12 +1135,9 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
 
   // rig constants, the same quantities fuseflow_create derives (Eq. 4 relative poses,
   // Sec. II.5(2)b neighbour table, ray tables), staged in host statics
-  const int K = std::min<int>(params->k_views, n_cams);
-  const int k1 = K - 1;
   int32_t nbr[kMaxCams * kMaxK1];
   neighbour_table_fixed(extr, n_cams, k1, nbr);
   const double unit = params->depth_scale;
-  if (2ll * k1 * n_rays > kStaticMaxPairRays) return FUSEFLOW_ERR_CAPACITY;
   RigDev& rig = g_static_rig;
   build_rig(intr, extr, n_cams, params, nbr, k1, rig, g_static_rays, g_static_pray);
   const int nr = (int)n_rays;
