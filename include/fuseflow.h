@@ -37,7 +37,8 @@ typedef enum {
     FUSEFLOW_ERR_CAPACITY = 3,      /* more cells than max_cells, or a hash table filled up */
     FUSEFLOW_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     FUSEFLOW_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
-    FUSEFLOW_ERR_INTERNAL = 6       /* a device-side consistency check failed */
+    FUSEFLOW_ERR_INTERNAL = 6,      /* a device-side consistency check failed */
+    FUSEFLOW_ERR_CANCELLED = 7      /* a served frame dropped before it started (rig removed) */
 } fuseflow_status;
 
 typedef enum {
@@ -168,6 +169,51 @@ int fuseflow_graph_create(fuseflow_ctx *ctx, const void *const *depth, const flo
 /* Enqueues the recorded frame on `stream`; *out (may be NULL) as for fuseflow_fuse_frame. */
 int fuseflow_graph_launch(fuseflow_graph *graph, fuseflow_cloud *out, void *stream);
 void fuseflow_graph_destroy(fuseflow_graph *graph);
+
+/* The context's output arrays (device pointers, as fuseflow_fuse_frame returns them); they
+ * hold the last frame fused on the context once the stream has reached that call. */
+int fuseflow_get_cloud(const fuseflow_ctx *ctx, fuseflow_cloud *out);
+
+/* Batched fusion (engineering entry points; frames are independent, Sec. I and II.1, so
+ * fusing several at once changes no result).  A batch holds up to FUSEFLOW_MAX_BATCH
+ * contexts (frames of one rig in several contexts, or of different rigs with any camera
+ * counts and resolutions) that share the depth format and top_k and have no depth screen
+ * set.  fuseflow_batch_fuse fuses one frame per context with every frame kernel launched
+ * ONCE for all of them: the frames' blocks share each grid (count and assign grids
+ * concatenate the frames' blocks; the others take the frame from the grid's second
+ * dimension), so short kernels run once per batch and frames fill each other's tails.
+ * depth[i], conf[i], rgb[i] are context i's per-camera device images (as for
+ * fuseflow_fuse_frame); each context's cloud and statistics are then read with its usual
+ * calls (fuseflow_get_cloud, fuseflow_read_stats) and are bitwise those of
+ * fuseflow_fuse_frame on that context.  The contexts must not be used elsewhere while a
+ * batch call runs; the batch holds pointers to them and does not own them.
+ * fuseflow_batch_graph_create records one batch call on fixed input buffers as a CUDA
+ * graph (replayed with fuseflow_graph_launch, whose cloud argument receives context 0's).
+ * Returns INVALID_ARG (count, mixed formats or variants, a screen, a repeated context,
+ * NULL pointers), OUT_OF_MEMORY, CUDA. */
+#define FUSEFLOW_MAX_BATCH 8
+typedef struct fuseflow_batch fuseflow_batch;
+int fuseflow_batch_create(fuseflow_ctx *const *ctxs, int32_t n, fuseflow_batch **out);
+int fuseflow_batch_fuse(fuseflow_batch *batch, const void *const *const *depth,
+                        const float *const *const *conf, const uint8_t *const *const *rgb,
+                        void *stream);
+int fuseflow_batch_graph_create(fuseflow_batch *batch, const void *const *const *depth,
+                                const float *const *const *conf, const uint8_t *const *const *rgb,
+                                fuseflow_graph **out);
+void fuseflow_batch_destroy(fuseflow_batch *batch);
+
+/* Point-wise fusion, the "No SA" ablation of Table II (fusion without the spatial hash,
+ * Sec. IV ablations): every gated pixel of the frame is an output point with its own joint
+ * weight omega = C V of Eq. 10, its consistency V computed over the camera's K-1 views
+ * exactly as in fuseflow_fuse_frame (Eq. 4-8).  Outputs are caller-owned DEVICE arrays
+ * indexed by the global pixel index g (n_pixels entries): pos[g][3] in metres (NaN when
+ * the pixel is not gated), weight[g] (0 when not gated; may underflow to 0 in float32),
+ * rgb_out[g][3] the pixel's 8-bit colour.  n_valid and n_gated (either may be NULL)
+ * receive the frame's counts, which synchronizes `stream`; with both NULL the call is
+ * asynchronous.  A context with a depth screen set is refused (INVALID_ARG). */
+int fuseflow_fuse_points(fuseflow_ctx *ctx, const void *const *depth, const float *const *conf,
+                         const uint8_t *const *rgb, float *pos, float *weight, uint8_t *rgb_out,
+                         int64_t *n_valid, int64_t *n_gated, void *stream);
 
 /* Waits for `stream`, copies the last frame's statistics to *host_stats and returns
  * CAPACITY if the frame overflowed max_cells or a hash table, INTERNAL if a device-side
@@ -342,12 +388,13 @@ int fuseflow_fuse_frame_static(const fuseflow_intrinsics *intr, const fuseflow_e
  *
  * The paper fuses the frames of one rig as a real-time stream (Sec. I, Sec. II.1); a
  * server here keeps several rigs resident on one GPU and overlaps their frames.  Each
- * rig gets n_slots frame slots, each with its own device tables, input staging buffers
- * and stream; the slots of all rigs are allocated up front against an HBM budget.  A
- * submitted frame starts at once when one of its rig's slots is free, otherwise it waits
- * and starts as soon as fuseflow_server_poll finds a slot of its rig finished (among the
- * waiting frames whose rig has a free slot, the one submitted first starts first), so the
- * copies and kernels of frames of different rigs and slots overlap on the device.
+ * rig has up to n_slots frame slots, each with its own device tables, input staging
+ * buffers and stream, allocated against an HBM budget as frames need them (see
+ * fuseflow_server_add_rig).  A submitted frame starts at once when one of its rig's slots
+ * is free or a new one fits in the budget, otherwise it waits and starts as soon as
+ * fuseflow_server_poll finds a slot of its rig finished (among the waiting frames whose
+ * rig can take one, the one submitted first starts first), so the copies and kernels of
+ * frames of different rigs and slots overlap on the device.
  * Results do not depend on the mix: every frame runs the same kernels on its own tables.
  * Each slot has a stream of its own: with many slots, set CUDA_DEVICE_MAX_CONNECTIONS=32
  * in the environment before the process initialises CUDA, since streams that share one
@@ -369,6 +416,23 @@ typedef struct {
     int64_t capacity;
 } fuseflow_host_cloud;
 
+/* Counters of a server (fuseflow_server_get_stats). */
+typedef struct {
+    int64_t budget_bytes;           /* the HBM budget */
+    int64_t used_bytes;             /* device bytes held by the slots */
+    int32_t rigs;                   /* resident rigs */
+    int32_t slots;                  /* frame slots allocated over all rigs */
+    int32_t inflight;               /* frames on the device */
+    int32_t waiting;                /* frames submitted and not started */
+    int64_t frames_submitted;
+    int64_t frames_completed;       /* reported by poll after running on a slot */
+    int64_t frames_failed;          /* reported by poll with the status of a failed start */
+    int64_t frames_cancelled;       /* reported by poll with CANCELLED (their rig was removed) */
+    int64_t deferred_by_budget;     /* frames that found every slot of their rig busy while the
+                                       rig held fewer slots than it asked for, and waited */
+    int64_t slots_grown;            /* slots allocated (including each rig's first) */
+} fuseflow_server_stats;
+
 /* One finished frame, reported by fuseflow_server_poll. */
 typedef struct {
     int64_t request;        /* id returned by fuseflow_server_submit */
@@ -381,29 +445,57 @@ typedef struct {
  * device memory for its rigs' slots (> 0).  Returns INVALID_ARG, OUT_OF_MEMORY. */
 int fuseflow_server_create(int64_t hbm_budget_bytes, fuseflow_server **out);
 
-/* Adds a rig (as fuseflow_create) with n_slots >= 1 frame slots; *rig_id receives its id.
- * With several slots the frames of the rig run with programmatic = 0 (fuseflow_tuning):
+/* Adds a rig (as fuseflow_create) that asks for up to n_slots >= 1 frames in flight;
+ * *rig_id receives its id.  A slot is one frame's device working set (a context with its
+ * tables and outputs, and a staging buffer for the frame's images).  The rig's first slot
+ * is allocated now and kept while the rig is resident (its camera constants and hash
+ * tables stay on the device); fuseflow_server_reserve allocates more, as far as the budget
+ * allows, and a rig removal gives the freed memory to the rigs below their request, one
+ * slot per rig in turn.  Slots are never allocated while frames are served (an allocation
+ * synchronizes the device): a frame that finds every slot of its rig busy waits, and is
+ * counted as deferred by the budget when the rig holds fewer slots than it asked for.
+ * With n_slots > 1 the frames of the rig run with programmatic = 0 (fuseflow_tuning):
  * the slots' overlapping streams fill the kernel boundaries, and blocks waiting for an
  * earlier kernel would only hold back the other slots' work.
- * Returns CAPACITY, with nothing allocated, if the slots would exceed the budget. */
+ * Returns CAPACITY, with nothing allocated, if one slot does not fit in the budget. */
 int fuseflow_server_add_rig(fuseflow_server *srv, const fuseflow_intrinsics *intr,
                             const fuseflow_extrinsics *extr, int32_t n_cams,
                             const fuseflow_params *params, int32_t n_slots, int32_t *rig_id);
 
+/* Allocates slots of rig `rig` until it holds min(n_slots, its request) or the next one
+ * does not fit in the budget; *n_held (may be NULL) receives the slots it holds.  Calling
+ * it for every rig with n_slots = 2, 3, ... in turn shares a binding budget evenly.
+ * Returns INVALID_ARG (unknown or removed rig), OUT_OF_MEMORY, CUDA; a budget that stops
+ * the growth is not an error. */
+int fuseflow_server_reserve(fuseflow_server *srv, int32_t rig, int32_t n_slots, int32_t *n_held);
+
+/* Removes rig `rig`: its frames on the device are waited for and reported by the next
+ * fuseflow_server_poll with their own status, its waiting frames are reported there with
+ * FUSEFLOW_ERR_CANCELLED (their host buffers are free at once), its slots are released
+ * and the memory returns to the budget, where the rigs holding fewer slots than they asked
+ * for take it one slot per rig in turn (their waiting frames may then start).  The id is
+ * not reused; later calls naming it return INVALID_ARG.  Synchronous for that rig's frames. */
+int fuseflow_server_remove_rig(fuseflow_server *srv, int32_t rig);
+
 /* Submits one frame of rig `rig`: depth[i], conf[i], rgb[i] are HOST pointers (pinned
  * for asynchronous copies) and *out the host output arrays (pinned: the copy-out kernel
  * writes them through their mapped addresses); all stay valid and untouched until the
- * frame is reported complete.  Never blocks on the device.  *request receives the frame's
- * id.  Returns INVALID_ARG, or the status of a frame start that failed (as for
- * fuseflow_server_poll; that frame may be this one or an earlier waiting one). */
+ * frame is reported complete.  On systems where the GPU reaches pageable host memory
+ * directly (Grace-based nodes) the server cannot tell pinned memory from any other host
+ * address, so the arrays must be valid host memory of the stated size: an invalid address
+ * is written by the device there.  Never blocks on the device.  *request receives the frame's
+ * id; every accepted frame is reported exactly once by fuseflow_server_poll.  Returns
+ * INVALID_ARG (the frame is then not accepted). */
 int fuseflow_server_submit(fuseflow_server *srv, int32_t rig, const void *const *depth,
                            const float *const *conf, const uint8_t *const *rgb,
                            const fuseflow_host_cloud *out, int64_t *request);
 
-/* Non-blocking: reports up to max_done finished frames (in completion order) in done[],
- * their number in *n_done, and starts waiting frames on the slots that became free.  A
- * waiting frame whose start fails (a CUDA error, host arrays that are not pinned) is
- * dropped without a completion, and the first such status is returned. */
+/* Non-blocking: reports up to max_done finished frames in done[], their number in
+ * *n_done, and starts waiting frames on the slots that became free.  A frame whose start
+ * failed (host output arrays that are not pinned, a CUDA error) is reported with that
+ * status, and only once every copy already queued from its host buffers has finished, so
+ * that the caller may reuse them; frames of a removed rig are reported as described for
+ * fuseflow_server_remove_rig.  Returns INVALID_ARG for bad arguments, else OK. */
 int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_t max_done,
                          int32_t *n_done);
 
@@ -411,8 +503,19 @@ int fuseflow_server_poll(fuseflow_server *srv, fuseflow_completion *done, int32_
  * takes a frame).  Waiting frames start in submission order across rigs, each as soon as
  * a slot of its rig is free and the cap allows; a lower cap gives each frame more of the
  * GPU and shortens the latency tail when many frames arrive together, at some loss of
- * overlap.  Returns INVALID_ARG for a negative cap, else as fuseflow_server_poll. */
+ * overlap.  Returns INVALID_ARG for a negative cap, else OK. */
 int fuseflow_server_set_max_inflight(fuseflow_server *srv, int32_t max_inflight);
+
+/* Testing hook for the server's error paths (made on the host; no GPU fault is involved):
+ * the next n frame starts fail with `status` (not OK), either before anything is queued
+ * (after_copies = 0) or after the frame's image copies were queued (after_copies = 1; the
+ * frame is then reported once those copies have finished).  n = 0 clears it.  Returns
+ * INVALID_ARG for bad arguments. */
+int fuseflow_server_inject_start_failure(fuseflow_server *srv, int32_t n, int32_t status,
+                                         int32_t after_copies);
+
+/* The server's counters (memory, slots, frames and deferrals). */
+int fuseflow_server_get_stats(const fuseflow_server *srv, fuseflow_server_stats *out);
 
 /* Frames submitted but not yet reported by fuseflow_server_poll. */
 int64_t fuseflow_server_pending(const fuseflow_server *srv);

@@ -55,6 +55,11 @@ struct fuseflow_ctx {
   long long timed_frames = 0;
 };
 
+// Contexts fused together by one launch of each frame kernel (launch_batch).
+struct fuseflow_batch {
+  std::vector<fuseflow_ctx*> ctx;
+};
+
 // One fuse call captured as a CUDA graph (the memset and kernels of launch_frame).
 struct fuseflow_graph {
   fuseflow_ctx* ctx = nullptr;
@@ -295,6 +300,7 @@ const char* fuseflow_status_string(int s) {
     case FUSEFLOW_ERR_CUDA: return "CUDA runtime error";
     case FUSEFLOW_ERR_TIMEOUT: return "device wait timed out";
     case FUSEFLOW_ERR_INTERNAL: return "internal device check failed";
+    case FUSEFLOW_ERR_CANCELLED: return "cancelled before it started (its rig was removed)";
     default: return "unknown status";
   }
 }
@@ -486,7 +492,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
         cudaMemset(ctx->d_out, 0, ctx->out_bytes) != cudaSuccess ||
         launch_init_tables(t, ctx->max_slots, ctx->ccap, 0) != cudaSuccess ||
         prepare_launch(rig->depth_f32 != 0) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
+        cudaStreamSynchronize(0) != cudaSuccess)     // this context's set-up only: work on
+                                                     // non-blocking streams keeps running
       status = FUSEFLOW_ERR_CUDA;
   }
   delete rig;
@@ -561,6 +568,95 @@ int fuseflow_graph_create(fuseflow_ctx* ctx, const void* const* depth, const flo
   } else {
     const cudaError_t e = launch_frame(ctx->d_rig, ctx->d_rays, fp, ctx->tab, ctx->trace, ctx->out,
                                        ctx->geo, s, nullptr);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g->graph ||
+        cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+      st = FUSEFLOW_ERR_CUDA;
+  }
+  if (s) cudaStreamDestroy(s);
+  if (st != FUSEFLOW_OK) {
+    cudaGetLastError();
+    fuseflow_graph_destroy(g);
+    return st;
+  }
+  *out = g;
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_get_cloud(const fuseflow_ctx* ctx, fuseflow_cloud* out) {
+  if (!ctx || !out) return FUSEFLOW_ERR_INVALID_ARG;
+  fill_cloud(ctx, out);
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_batch_create(fuseflow_ctx* const* ctxs, int32_t n, fuseflow_batch** out) {
+  if (!out) return FUSEFLOW_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctxs || n < 1 || n > kMaxBatch) return FUSEFLOW_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->geo.screen || ctxs[i]->device != ctxs[0]->device ||
+        ctxs[i]->geo.depth_f32 != ctxs[0]->geo.depth_f32 || ctxs[i]->geo.top_k != ctxs[0]->geo.top_k)
+      return FUSEFLOW_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return FUSEFLOW_ERR_INVALID_ARG;   // one frame per context
+  }
+  fuseflow_batch* b = new (std::nothrow) fuseflow_batch();
+  if (!b) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  b->ctx.assign(ctxs, ctxs + n);
+  *out = b;
+  return FUSEFLOW_OK;
+}
+
+void fuseflow_batch_destroy(fuseflow_batch* b) { delete b; }
+
+// The frames of a batch call: each context's images, tables and geometry (no trace).
+static int batch_frames(const fuseflow_batch* b, const void* const* const* depth,
+                        const float* const* const* conf, const uint8_t* const* const* rgb,
+                        FrameLaunch* fl) {
+  if (!b || !depth || !conf || !rgb) return FUSEFLOW_ERR_INVALID_ARG;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    const fuseflow_ctx* c = b->ctx[i];
+    int ok = 0;
+    fl[i].fp = frame_ptrs(c, depth[i], conf[i], rgb[i], &ok);
+    if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
+    fl[i].rig = c->d_rig;
+    fl[i].rays = c->d_rays;
+    fl[i].t = c->tab;
+    fl[i].tr = TraceDev{};
+    fl[i].out = c->out;
+    fl[i].geo = &c->geo;
+  }
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_batch_fuse(fuseflow_batch* b, const void* const* const* depth, const float* const* const* conf,
+                        const uint8_t* const* const* rgb, void* stream) {
+  FrameLaunch fl[kMaxBatch];
+  const int st = batch_frames(b, depth, conf, rgb, fl);
+  if (st != FUSEFLOW_OK) return st;
+  return launch_batch(fl, (int)b->ctx.size(), static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FUSEFLOW_OK : FUSEFLOW_ERR_CUDA;
+}
+
+int fuseflow_batch_graph_create(fuseflow_batch* b, const void* const* const* depth,
+                                const float* const* const* conf, const uint8_t* const* const* rgb,
+                                fuseflow_graph** out) {
+  if (!out) return FUSEFLOW_ERR_INVALID_ARG;
+  *out = nullptr;
+  FrameLaunch fl[kMaxBatch];
+  int st = batch_frames(b, depth, conf, rgb, fl);
+  if (st != FUSEFLOW_OK) return st;
+  fuseflow_graph* g = new (std::nothrow) fuseflow_graph();
+  if (!g) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  g->ctx = b->ctx[0];
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    s = nullptr;
+    st = FUSEFLOW_ERR_CUDA;
+  } else if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    st = FUSEFLOW_ERR_CUDA;
+  } else {
+    const cudaError_t e = launch_batch(fl, (int)b->ctx.size(), s);
     const cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
     if (e != cudaSuccess || e2 != cudaSuccess || !g->graph ||
         cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
@@ -708,6 +804,19 @@ int fuseflow_confidence(fuseflow_ctx* ctx, const void* const* depth, float* cons
              ? FUSEFLOW_OK : FUSEFLOW_ERR_CUDA;
 }
 
+// Small per-context device buffers, allocated on first use: the per-block sums of the MC
+// error (kMcBytes) followed by the two counters of the point-wise path.
+constexpr size_t kMcBytes = 1024 * (sizeof(double) + sizeof(long long));
+static bool small_buffers(fuseflow_ctx* ctx) {
+  if (ctx->d_mc) return true;
+  if (cudaMalloc(&ctx->d_mc, kMcBytes + 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    ctx->d_mc = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 int fuseflow_mc_error(fuseflow_ctx* ctx, const float* pos, int64_t n_points,
                       const void* const* depth, double occlusion_m, float* err_m,
                       int32_t* n_visible, double* mc_m, int64_t* n_used, void* stream) {
@@ -717,10 +826,7 @@ int fuseflow_mc_error(fuseflow_ctx* ctx, const float* pos, int64_t n_points,
   for (int i = 0; i < ctx->n_cams; ++i)
     if (!depth[i]) return FUSEFLOW_ERR_INVALID_ARG;
   const int blocks = ffl::mc_blocks(n_points);
-  if (!ctx->d_mc && cudaMalloc(&ctx->d_mc, 1024 * (sizeof(double) + sizeof(long long))) != cudaSuccess) {
-    ctx->d_mc = nullptr;
-    return FUSEFLOW_ERR_OUT_OF_MEMORY;
-  }
+  if (!small_buffers(ctx)) return FUSEFLOW_ERR_OUT_OF_MEMORY;
   double* bsum = static_cast<double*>(ctx->d_mc);
   long long* bcnt = reinterpret_cast<long long*>(bsum + 1024);
   FramePtrs fp{};
@@ -739,6 +845,33 @@ int fuseflow_mc_error(fuseflow_ctx* ctx, const float* pos, int64_t n_points,
   for (int b = 0; b < blocks; ++b) { sum += hs[b]; cnt += hc[b]; }
   *n_used = cnt;
   *mc_m = cnt ? sum / (double)cnt * ctx->params.depth_scale : std::nan("");
+  return FUSEFLOW_OK;
+}
+
+int fuseflow_fuse_points(fuseflow_ctx* ctx, const void* const* depth, const float* const* conf,
+                         const uint8_t* const* rgb, float* pos, float* weight, uint8_t* rgb_out,
+                         int64_t* n_valid, int64_t* n_gated, void* stream) {
+  if (!ctx || !pos || !weight || !rgb_out) return FUSEFLOW_ERR_INVALID_ARG;
+  if (ctx->geo.screen) return FUSEFLOW_ERR_INVALID_ARG;          // D^r is not applied here
+  int ok = 0;
+  const FramePtrs fp = frame_ptrs(ctx, depth, conf, rgb, &ok);
+  if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
+  if (!small_buffers(ctx)) return FUSEFLOW_ERR_OUT_OF_MEMORY;
+  PointsDev pd{pos, weight, rgb_out,
+               reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->d_mc) + kMcBytes),
+               (float)ctx->params.depth_scale};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (launch_points(ctx->d_rig, ctx->d_rays, fp, ctx->tab, pd, ctx->geo.depth_f32 != 0, ctx->n_cams,
+                    ctx->geo.max_px, s) != cudaSuccess)
+    return FUSEFLOW_ERR_CUDA;
+  if (n_valid || n_gated) {
+    unsigned long long h[2] = {0ull, 0ull};
+    if (cudaMemcpyAsync(h, pd.counts, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return FUSEFLOW_ERR_CUDA;
+    if (n_valid) *n_valid = (int64_t)h[0];
+    if (n_gated) *n_gated = (int64_t)h[1];
+  }
   return FUSEFLOW_OK;
 }
 

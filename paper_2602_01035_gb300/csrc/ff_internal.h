@@ -66,6 +66,37 @@ struct OutDev {
 // Assign-step prefetch distance (tiles) that turns the L2 prefetch off.
 constexpr int kNoPrefetch = 1 << 30;
 
+// Everything the frame kernels need about one frame: the rig constants, its images, its
+// tables and outputs, its tile index and count-step geometry.
+struct FrameArgs {
+  const RigDev* rig;
+  const float2* rays;
+  FramePtrs fp;
+  Tables t;
+  TraceDev tr;
+  OutDev out;
+  TileIndex ti;
+  int count_blocks_x, count_chunks;
+  float unit_m;
+  int pad;
+};
+
+// Frames of one launch of the frame kernels, passed as one __grid_constant__ kernel
+// parameter (kernel parameter space holds up to 32,764 bytes).  One-dimensional grids
+// (count, assign) concatenate the frames' blocks: frame f owns blocks
+// [count_first[f], count_first[f + 1]) of the count grid and [tile_first[f],
+// tile_first[f + 1]) of the assign grid; the other kernels take the frame from blockIdx.y.
+// NB = 1 is the plain one-frame launch (frame index 0, a compile-time constant).
+constexpr int kMaxBatch = FUSEFLOW_MAX_BATCH;
+template <int NB>
+struct BatchArgs {
+  int n;
+  int count_first[NB + 1];
+  int tile_first[NB + 1];
+  FrameArgs f[NB];
+};
+static_assert(sizeof(BatchArgs<kMaxBatch>) <= 32764, "a batch fits in kernel parameter space");
+
 // Depth preprocessing D^r of Eq. 8: range screen in depth units, then the edge screen
 // against valid in-range 4-neighbours (bounds and ratio <= 0 are off).
 struct ScreenArgs {
@@ -128,6 +159,19 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
                       long long n, double unit_m, double occlusion_m, float* err, int* nvis,
                       double* bsum, long long* bcnt, cudaStream_t s);
 
+// Point-wise fusion (Table II "No SA"): per global pixel index, the position (metres), the
+// joint weight and the colour; counts[0..1] = valid and gated pixels of the frame.
+struct PointsDev {
+  float* pos;
+  float* weight;
+  uint8_t* rgb;
+  unsigned long long* counts;
+  float unit_f;
+};
+cudaError_t launch_points(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
+                          const PointsDev& out, bool depth_f32, int n_cams, long long max_px,
+                          cudaStream_t s);
+
 // Eq. 3 confidence producer: per camera, depth in, float32 confidence out.
 struct ConfArgs {
   const void* depth[kMaxCams];
@@ -147,6 +191,20 @@ void fill_block_consts(const RigDev& rig, BlockConst* out);
 // Kernel attributes a frame's launches need (called by context creation, so that a later
 // stream capture of launch_frame makes no attribute call).
 cudaError_t prepare_launch(bool depth_f32);
+// One frame of a launch (host side): rig constants, images, tables, trace, outputs and the
+// launch geometry of its context.
+struct FrameLaunch {
+  const RigDev* rig;
+  const float2* rays;
+  FramePtrs fp;
+  Tables t;
+  TraceDev tr;
+  OutDev out;
+  const Geometry* geo;
+};
+// n <= kMaxBatch frames (one depth type, one fusion variant) with every frame kernel
+// launched once for all of them: the frames' blocks share each grid.
+cudaError_t launch_batch(const FrameLaunch* frames, int n, cudaStream_t s);
 // ev: NULL, or FUSEFLOW_N_STAGES + 1 events recorded before, between and after the stages
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp,
                          const Tables& t, const TraceDev& tr, const OutDev& out,

@@ -91,7 +91,24 @@ __device__ __forceinline__ unsigned coarse_lvbase(const Tables& t, unsigned long
 __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-__global__ void __launch_bounds__(kThreads) k_levels(Tables t) {
+// Frame of a block of a one-dimensional grid that concatenates the frames' blocks
+// (first[f] = the frame's first block), and the block's index within its frame.
+template <int NB>
+__device__ __forceinline__ int batch_frame(const int (&first)[NB + 1], int n, int b, int& local) {
+  int f = 0;
+#pragma unroll
+  for (int k = 1; k < NB; ++k)
+    if (k < n && b >= first[k]) f = k;
+  local = b - first[f];
+  return f;
+}
+// Frame of a block of a grid whose y dimension runs over the frames.
+template <int NB>
+__device__ __forceinline__ int batch_frame_y() { return NB == 1 ? 0 : (int)blockIdx.y; }
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads) k_levels(const __grid_constant__ BatchArgs<NB> args) {
+  const Tables& t = args.f[batch_frame_y<NB>()].t;
   pdl_release();
   pdl_wait();
   const unsigned n_coarse = min(t.cnt->n_coarse, t.cmask + 1u);
@@ -125,10 +142,18 @@ __global__ void __launch_bounds__(kThreads) k_levels(Tables t) {
 }
 
 // Block-local open addressing (shared memory); returns the table position or -1, and sets
-// `fresh` when this call inserted the key.
+// `fresh` when this call inserted the key.  32-bit keys (dense cell slots) take a
+// multiplicative (Fibonacci) hash, 64-bit keys (packed coarse keys) the 64-bit mixer.
 template <int TS, typename K>
 __device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe, bool& fresh) {
-  unsigned h = (unsigned)mix64((unsigned long long)key) & (TS - 1);
+  unsigned h;
+  if constexpr (sizeof(K) == 4) {
+    constexpr int kBits = TS == 1024 ? 10 : TS == 2048 ? 11 : TS == 4096 ? 12 : 0;
+    static_assert(kBits > 0, "block table size");
+    h = ((unsigned)key * 0x9E3779B1u) >> (32 - kBits);
+  } else {
+    h = (unsigned)mix64((unsigned long long)key) & (TS - 1);
+  }
   fresh = false;
   for (int probe = 0; probe < max_probe; ++probe) {
     const K cur = *static_cast<volatile K*>(&tab[h]);
@@ -365,28 +390,36 @@ __device__ __forceinline__ void count_add(const Tables& t, unsigned long long* s
   }
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(kThreads, 4)
-k_count(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
-        int blocks_x, int chunks) {
+template <typename DT, int NB>
+__global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ BatchArgs<NB> args) {
+  int local;
+  const FrameArgs& fa = args.f[batch_frame<NB>(args.count_first, args.n, (int)blockIdx.x, local)];
+  const RigDev* __restrict__ rigp = fa.rig;
+  const float2* __restrict__ rays = fa.rays;
+  const FramePtrs& fp = fa.fp;
+  const Tables& t = fa.t;
+  const int blocks_x = fa.count_blocks_x, chunks = fa.count_chunks;
+  const int cam = local / blocks_x, bx = local - cam * blocks_x;
   pdl_release();
   constexpr int TS = 2048;                                      // block table of coarse keys
   __shared__ unsigned long long s_key[TS];
   __shared__ unsigned s_cnt[TS];
   __shared__ unsigned s_fill;                                    // keys in the block table
   __shared__ unsigned short s_occ[TS];                           // occupied positions, packed
+  // the packing loop below walks the table in whole warps (every lane reaches the ballot)
+  // and stores positions as 16-bit values
+  static_assert(TS % kThreads == 0 && kThreads % 32 == 0 && TS <= 65536, "block table shape");
   __shared__ unsigned s_nocc;
   __shared__ unsigned s_red[kThreads / 32][9];
   const RigDev& rig = *rigp;
-  const int cam = blockIdx.y;
   // the camera's constants and the rig's scalars in registers (they would otherwise be
   // re-read for every pixel, as the atomics below may alias memory for the compiler)
   const CamDev C = rig.cam[cam];
   const float tau = rig.tau, inv_s0u = rig.inv_s0u;
   const int use_conf = rig.use_conf, lim = kKeyBias >> rig.max_level;
   const long long npx = (long long)C.W * C.H;
-  const int bid = cam * blocks_x + blockIdx.x;
-  const long long c0 = (long long)blockIdx.x * chunks;          // first chunk of 2048 pixels
+  const int bid = cam * blocks_x + bx;
+  const long long c0 = (long long)bx * chunks;                  // first chunk of 2048 pixels
   const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
   if (threadIdx.x == 0) { s_fill = 0u; s_nocc = 0u; }
@@ -652,10 +685,18 @@ __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, in
 // TOPK: the Sec. II.5(2)a variant; members are keyed and counted as usual, but a tile keeps
 // each cell's top-k members by C (packed (ordered(C) << 32) | ~g keys) instead of weights;
 // the consistency and weights of those members are computed per cell by k_reduce_topk.
-template <typename DT, bool TOPK, bool TRACE>
+template <typename DT, bool TOPK, bool TRACE, int NB>
 __global__ void __launch_bounds__(kAssignThreads, kAssignBlocksPerSM)
-k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, FramePtrs fp, Tables t,
-         TraceDev tr, float unit_m, TileIndex ti) {
+k_assign(const __grid_constant__ BatchArgs<NB> args) {
+  int T;
+  const FrameArgs& fa = args.f[batch_frame<NB>(args.tile_first, args.n, (int)blockIdx.x, T)];
+  const RigDev* __restrict__ rigp = fa.rig;
+  const float2* __restrict__ rays = fa.rays;
+  const FramePtrs& fp = fa.fp;
+  const Tables& t = fa.t;
+  const TraceDev& tr = fa.tr;
+  const float unit_m = (float)fa.unit_m;
+  const TileIndex& ti = fa.ti;
   pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   BlockConst& bc = *reinterpret_cast<BlockConst*>(smem + kSmBC);
@@ -676,7 +717,7 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
 
   const RigDev& rig = *rigp;
   int cam, x0, y0;
-  tile_of(ti, (int)blockIdx.x, cam, x0, y0);
+  tile_of(ti, T, cam, x0, y0);
   const int W = ti.W[cam], H = ti.H[cam], k1 = ti.k1;
   struct { int x0, y0; long long off; } td;
   td.x0 = x0;
@@ -684,9 +725,9 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   td.off = ti.off[cam];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // warm L2 with the images of the tile that starts when this wave of blocks has finished
-  if (threadIdx.x < 4 * kTileH && (int)blockIdx.x + ti.ahead < t.n_tiles) {
+  if (threadIdx.x < 4 * kTileH && T + ti.ahead < t.n_tiles) {
     int pc, px0, py0;
-    tile_of(ti, (int)blockIdx.x + ti.ahead, pc, px0, py0);
+    tile_of(ti, T + ti.ahead, pc, px0, py0);
     const int row = py0 + (threadIdx.x & (kTileH - 1)), kind = threadIdx.x / kTileH;
     if (row < ti.H[pc]) {                     // every address lies inside its image
       const long long li = (long long)row * ti.W[pc] + px0;
@@ -819,22 +860,6 @@ k_assign(const RigDev* __restrict__ rigp, const float2* __restrict__ rays, Frame
   // everything above read only the frame's inputs and the context's constants; the coarse
   // table (count and level steps) and every table written below need the earlier kernels
   pdl_wait();
-
-  // the second point's coarse record: start its lookup now (into L1), so that it arrives
-  // while the first point is processed
-  {
-    const int i = threadIdx.x + kAssignThreads;
-    if (i < n_g) {
-      const int pid = s_pid[i];
-      const int x = td.x0 + (pid & (kTileW - 1)), y = td.y0 + pid / kTileW;
-      float P[3], r[3];
-      world_point(C, s_z[i], __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);
-      if (grid_coords(rig, P, r)) {
-        const unsigned h = (unsigned)mix64(coarse_key(r)) & t.cmask;
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(&t.coarse[h]));
-      }
-    }
-  }
 
   // (a) Eq. 8, (b) Eq. 4-7 and 10, (c) Sec. II.5(1)d-e for each gated point
   bool has[2] = {false, false};
@@ -1107,7 +1132,10 @@ __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
   return __fmaf_rn(__uint2float_rn((unsigned)(x >> 32)), 4294967296.0f, __uint2float_rn((unsigned)x));
 }
 
-__global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
+template <int NB>
+__global__ void __launch_bounds__(kThreads) k_reduce(const __grid_constant__ BatchArgs<NB> args) {
+  const Tables& t = args.f[batch_frame_y<NB>()].t;
+  const OutDev& out = args.f[batch_frame_y<NB>()].out;
   pdl_release();
   pdl_wait();
   const unsigned n_cells = min(t.cnt->n_cells, t.max_slots);
@@ -1177,10 +1205,14 @@ __global__ void __launch_bounds__(kThreads) k_reduce(Tables t, OutDev out) {
 // global pair rays) and omega = C V (Eq. 10), and fuse them (Eq. 11, normalised, weights
 // scaled by the largest).  Members are counted over the whole cell; the representative is
 // the cell's top member.
-template <typename DT>
-__global__ void __launch_bounds__(kThreads) k_reduce_topk(const RigDev* __restrict__ rigp,
-                                                          const float2* __restrict__ rays,
-                                                          FramePtrs fp, Tables t, OutDev out) {
+template <typename DT, int NB>
+__global__ void __launch_bounds__(kThreads) k_reduce_topk(const __grid_constant__ BatchArgs<NB> args) {
+  const FrameArgs& fa = args.f[batch_frame_y<NB>()];
+  const RigDev* __restrict__ rigp = fa.rig;
+  const float2* __restrict__ rays = fa.rays;
+  const FramePtrs& fp = fa.fp;
+  const Tables& t = fa.t;
+  const OutDev& out = fa.out;
   pdl_release();
   pdl_wait();
   const RigDev& rig = *rigp;
@@ -1293,6 +1325,68 @@ __global__ void __launch_bounds__(kThreads) k_reduce_topk(const RigDev* __restri
   }
 }
 
+// ------------------------------------------------------------------ point-wise (No SA)
+// Table II's "No SA" ablation: fusion without the spatial hash, every gated pixel an output
+// point with its own joint weight.  Per pixel: Eq. 8-9 (gate, back-projection), Eq. 4-7 over
+// the camera's K-1 views (the same double-float evaluation and global pair rays as the
+// top-k reduce step) and Eq. 10; outputs are indexed by the global pixel index (position in
+// metres and weight; NaN position and weight 0 for pixels that are not gated, 8-bit colour
+// copied), so the cloud is in pixel order without a compaction pass.  One thread a pixel,
+// cameras along the grid's second dimension.
+template <typename DT>
+__global__ void __launch_bounds__(kThreads) k_points(const RigDev* __restrict__ rigp,
+                                                     const float2* __restrict__ rays, FramePtrs fp,
+                                                     Tables t, PointsDev out) {
+  const RigDev& rig = *rigp;
+  const int cam = blockIdx.y;
+  const CamDev& C = rig.cam[cam];
+  const long long npx = (long long)C.W * C.H;
+  const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
+  const float* __restrict__ cf = fp.conf[cam];
+  const uint8_t* __restrict__ col = fp.rgb[cam];
+  const float qnan = __int_as_float(0x7fc00000);
+  unsigned nv = 0u, ng = 0u;
+  for (long long li = (long long)blockIdx.x * blockDim.x + threadIdx.x; li < npx;
+       li += (long long)gridDim.x * blockDim.x) {
+    const long long g = C.off + li;
+    const DT D = dep[li];
+    const float c = cf[li];
+    const bool valid = Depth<DT>::valid(D);
+    const bool gated = valid && (!rig.use_conf || c > rig.tau);          // Eq. 9
+    nv += valid ? 1u : 0u;
+    ng += gated ? 1u : 0u;
+    out.rgb[3 * g] = col[3 * li];
+    out.rgb[3 * g + 1] = col[3 * li + 1];
+    out.rgb[3 * g + 2] = col[3 * li + 2];
+    if (!gated) {
+      out.pos[3 * g] = qnan;
+      out.pos[3 * g + 1] = qnan;
+      out.pos[3 * g + 2] = qnan;
+      out.weight[g] = 0.0f;
+      continue;
+    }
+    const int y = (int)(li / C.W), x = (int)(li - (long long)y * C.W);
+    const float z = Depth<DT>::z(D);
+    float P[3];
+    world_point(C, z, __ldg(&rays[C.ray_x + x].x), __ldg(&rays[C.ray_y + y].x), P);   // Eq. 8
+    float sh = 0.0f, sl = 0.0f, mu;
+    int nview = 0, m;
+    if (rig.use_cons && rig.k1 > 0)
+      residual_sum<DT>(t.bconst[cam], rig.k1, GlobalPairRays{t.pray, x, y}, rays, fp, z, sh, sl, nview);
+    joint_weight(rig, rig.k1, sh, sl, c, mu, m);                          // Eq. 7, 10
+    out.pos[3 * g] = __fmul_rn(P[0], out.unit_f);
+    out.pos[3 * g + 1] = __fmul_rn(P[1], out.unit_f);
+    out.pos[3 * g + 2] = __fmul_rn(P[2], out.unit_f);
+    out.weight[g] = ldexpf(mu, -min(m, 1 << 30));
+  }
+  nv = __reduce_add_sync(0xffffffffu, nv);
+  ng = __reduce_add_sync(0xffffffffu, ng);
+  if ((threadIdx.x & 31) == 0) {
+    if (nv) atomicAdd(&out.counts[0], (unsigned long long)nv);
+    if (ng) atomicAdd(&out.counts[1], (unsigned long long)ng);
+  }
+}
+
 // ------------------------------------------------------------------ scan + stats
 __device__ __forceinline__ unsigned block_excl_scan_1024(unsigned v, unsigned* s_w, unsigned& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1323,13 +1417,18 @@ __device__ __forceinline__ unsigned block_excl_scan_1024(unsigned v, unsigned* s
 // Block b scans bitmap words [1024 b, 1024 b + 1024) and folds a share of the count step's
 // per-block statistics into the frame counters; the last block to finish (a fenced
 // counter, no waiting) scans the per-block sums and writes the frame statistics.
-__global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
+template <int NB>
+__global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ BatchArgs<NB> args) {
   __shared__ unsigned s_w[32];
   __shared__ unsigned long long s_l[3][32];
   __shared__ unsigned s_b[6][32];
   __shared__ bool s_last;
+  const Tables& t = args.f[batch_frame_y<NB>()].t;
+  const OutDev& out = args.f[batch_frame_y<NB>()].out;
+  const unsigned nblk = (unsigned)t.n_wblocks;     // this frame's blocks (the grid may be wider)
   pdl_release();
   pdl_wait();
+  if (blockIdx.x >= nblk) return;                  // uniform over the block
   const long long w = (long long)blockIdx.x * 1024 + threadIdx.x;
   const unsigned v = (w < t.n_words) ? __popc(t.bitmap[w]) : 0u;
   unsigned total;
@@ -1338,7 +1437,7 @@ __global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
   if (threadIdx.x == 0) t.bsum[blockIdx.x] = total;
 
   // statistics of the count step's blocks [b0, b1)
-  const int per = (t.n_bstats + gridDim.x - 1) / gridDim.x;
+  const int per = (t.n_bstats + (int)nblk - 1) / (int)nblk;
   const int b0 = blockIdx.x * per, b1 = min(t.n_bstats, b0 + per);
   unsigned long long nv = 0, ng = 0, noor = 0;
   unsigned bmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, bmax[3] = {0u, 0u, 0u};
@@ -1379,7 +1478,7 @@ __global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
       if (mx[k] != 0u) atomicMax(&t.cnt->bmax[k], mx[k]);
     }
     __threadfence();
-    s_last = atomicAdd(&t.cnt->scan_done, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&t.cnt->scan_done, 1u) == nblk - 1;
   }
   __syncthreads();
   if (!s_last) return;
@@ -1417,7 +1516,10 @@ __global__ void __launch_bounds__(1024) k_scan(Tables t, OutDev out) {
 }
 
 // ------------------------------------------------------------------ emit
-__global__ void __launch_bounds__(kThreads) k_emit(Tables t, OutDev out) {
+template <int NB>
+__global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ BatchArgs<NB> args) {
+  const Tables& t = args.f[batch_frame_y<NB>()].t;
+  const OutDev& out = args.f[batch_frame_y<NB>()].out;
   pdl_release();
   pdl_wait();
   const unsigned n_cells = (unsigned)min((long long)min(t.cnt->n_cells, t.max_slots), out.max_cells);
@@ -1815,13 +1917,13 @@ cudaError_t set_assign_attributes() {
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   const int sm = (int)assign_smem(kMaxK1);
-  cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_assign<DT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_assign<DT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_assign<DT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false, 1>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, true, 1>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, 1>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, true, 1>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, false, kMaxBatch>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, kMaxBatch>, at, sm);
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
   return e;
 }
@@ -1844,60 +1946,92 @@ cudaError_t launch_k(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, size
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename DT>
-cudaError_t launch_typed(const RigDev* rig, const float2* rays, const FramePtrs& fp_in, const Tables& t,
-                         const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
-                         cudaEvent_t* ev) {
+// The frame kernels over n frames (NB = 1: one frame; NB = kMaxBatch: a batch of up to
+// that many frames of any rigs, every kernel launched once for all of them).
+template <typename DT, int NB>
+cudaError_t launch_frames(const FrameLaunch* fr, int n, cudaStream_t s, cudaEvent_t* ev) {
   const cudaError_t ae = set_assign_attributes<DT>();
   if (ae != cudaSuccess) return ae;
+  if (n < 1 || n > NB) return cudaErrorInvalidValue;
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
-  cudaError_t err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
-  if (err != cudaSuccess) return err;
-  FramePtrs fp = fp_in;
-  if (geo.screen) {                        // D^r of Eq. 8 into the context's buffers
-    ScreenArgs a = geo.scr;
-    for (int i = 0; i < geo.n_cams; ++i) {
-      a.in[i] = fp_in.depth[i];
-      fp.depth[i] = a.out[i];
+  static thread_local BatchArgs<NB> a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  int emit = 1, pdl_level = 2, max_wblocks = 1, max_k1 = 0;
+  const Geometry& g0 = *fr[0].geo;
+  cudaError_t err = cudaSuccess;
+  for (int f = 0; f < n; ++f) {
+    const Geometry& geo = *fr[f].geo;
+    const Tables& t = fr[f].t;
+    err = cudaMemsetAsync(t.cnt, 0, sizeof(FrameCounters) + sizeof(unsigned) * (size_t)t.n_words, s);
+    if (err != cudaSuccess) return err;
+    FrameArgs& fa = a.f[f];
+    fa.rig = fr[f].rig;
+    fa.rays = fr[f].rays;
+    fa.fp = fr[f].fp;
+    fa.t = t;
+    fa.tr = fr[f].tr;
+    fa.out = fr[f].out;
+    fa.ti = geo.tiles;
+    fa.count_blocks_x = geo.count_blocks_x;
+    fa.count_chunks = geo.count_chunks;
+    fa.unit_m = (float)fr[f].out.unit_m;
+    if (geo.screen) {                      // D^r of Eq. 8 into the context's buffers
+      ScreenArgs sa = geo.scr;
+      for (int i = 0; i < geo.n_cams; ++i) {
+        sa.in[i] = fr[f].fp.depth[i];
+        fa.fp.depth[i] = sa.out[i];
+      }
+      if ((err = launch_screen(sa, sizeof(DT) == 4, geo.max_px, s)) != cudaSuccess) return err;
     }
-    if ((err = launch_screen(a, sizeof(DT) == 4, geo.max_px, s)) != cudaSuccess) return err;
+    a.count_first[f + 1] = a.count_first[f] + geo.count_blocks_x * geo.n_cams;
+    a.tile_first[f + 1] = a.tile_first[f] + t.n_tiles;
+    emit = std::max(emit, geo.emit_blocks);
+    pdl_level = std::min(pdl_level, geo.pdl);
+    max_wblocks = std::max(max_wblocks, t.n_wblocks);
+    max_k1 = std::max(max_k1, geo.tiles.k1);
   }
   mark(1);
-  // programmatic launches between the frame's kernels when the geometry asks for them
-  // (level 2 also between the assign and reduce steps), never while stage events are
-  // recorded between them
-  const bool pdl = geo.pdl >= 1 && ev == nullptr;
-  const bool pdl_reduce = geo.pdl >= 2 && ev == nullptr;
-  const float um = (float)out.unit_m;
-  if ((err = launch_k(false, k_count<DT>, dim3(geo.count_blocks_x, geo.n_cams), dim3(kThreads), 0, s, rig, rays,
-                      fp, t, geo.count_blocks_x, geo.count_chunks)) != cudaSuccess ||
-      (err = launch_k(pdl, k_levels, dim3(geo.emit_blocks), dim3(kThreads), 0, s, t)) != cudaSuccess)
+  // programmatic launches between the kernels when the geometry asks for them (level 2
+  // also between the assign and reduce steps), never while stage events are recorded
+  const bool pdl = pdl_level >= 1 && ev == nullptr;
+  const bool pdl_reduce = pdl_level >= 2 && ev == nullptr;
+  const dim3 eb(emit, n), th(kThreads);
+  if ((err = launch_k(false, k_count<DT, NB>, dim3(a.count_first[n]), th, 0, s, a)) != cudaSuccess ||
+      (err = launch_k(pdl, k_levels<NB>, eb, th, 0, s, a)) != cudaSuccess)
     return err;
   mark(2);
-  const bool traced = tr.pw || tr.omega || tr.e || tr.nview || tr.key;
-  const dim3 tiles(t.n_tiles), at(kAssignThreads), eb(geo.emit_blocks), th(kThreads);
-  if (geo.top_k) {
-    err = traced ? launch_k(pdl, k_assign<DT, true, true>, tiles, at, assign_smem(0), s, rig, rays, fp, t, tr, um,
-                            geo.tiles)
-                 : launch_k(pdl, k_assign<DT, true, false>, tiles, at, assign_smem(0), s, rig, rays, fp, t, tr, um,
-                            geo.tiles);
+  bool traced = false;
+  for (int f = 0; f < n; ++f) {
+    const TraceDev& tr = fr[f].tr;
+    traced = traced || tr.pw || tr.omega || tr.e || tr.nview || tr.key;
+  }
+  const dim3 tiles(a.tile_first[n]), at(kAssignThreads);
+  if (g0.top_k) {
+    if constexpr (NB == 1)
+      err = traced ? launch_k(pdl, k_assign<DT, true, true, NB>, tiles, at, assign_smem(0), s, a)
+                   : launch_k(pdl, k_assign<DT, true, false, NB>, tiles, at, assign_smem(0), s, a);
+    else
+      err = launch_k(pdl, k_assign<DT, true, false, NB>, tiles, at, assign_smem(0), s, a);
     if (err != cudaSuccess) return err;
     mark(3);
-    if ((err = launch_k(pdl_reduce, k_reduce_topk<DT>, eb, th, 0, s, rig, rays, fp, t, out)) != cudaSuccess)
-      return err;
+    if ((err = launch_k(pdl_reduce, k_reduce_topk<DT, NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
   } else {
-    const size_t sm = assign_smem(geo.tiles.k1);
-    err = traced ? launch_k(pdl, k_assign<DT, false, true>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles)
-                 : launch_k(pdl, k_assign<DT, false, false>, tiles, at, sm, s, rig, rays, fp, t, tr, um, geo.tiles);
+    const size_t sm = assign_smem(max_k1);
+    if constexpr (NB == 1)
+      err = traced ? launch_k(pdl, k_assign<DT, false, true, NB>, tiles, at, sm, s, a)
+                   : launch_k(pdl, k_assign<DT, false, false, NB>, tiles, at, sm, s, a);
+    else
+      err = launch_k(pdl, k_assign<DT, false, false, NB>, tiles, at, sm, s, a);
     if (err != cudaSuccess) return err;
     mark(3);
-    if ((err = launch_k(pdl_reduce, k_reduce, eb, th, 0, s, t, out)) != cudaSuccess) return err;
+    if ((err = launch_k(pdl_reduce, k_reduce<NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
   }
   mark(4);
-  if ((err = launch_k(pdl, k_scan, dim3(t.n_wblocks), dim3(1024), 0, s, t, out)) != cudaSuccess) return err;
+  if ((err = launch_k(pdl, k_scan<NB>, dim3(max_wblocks, n), dim3(1024), 0, s, a)) != cudaSuccess) return err;
   mark(5);
-  if ((err = launch_k(pdl, k_emit, eb, th, 0, s, t, out)) != cudaSuccess) return err;
+  if ((err = launch_k(pdl, k_emit<NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
   mark(6);
   return cudaGetLastError();
 }
@@ -1971,6 +2105,18 @@ cudaError_t launch_mc(const RigDev* rig, const FramePtrs& fp, bool depth_f32, co
   return cudaGetLastError();
 }
 
+cudaError_t launch_points(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
+                          const PointsDev& out, bool depth_f32, int n_cams, long long max_px,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out.counts, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const long long per = (max_px + kThreads - 1) / kThreads;
+  const dim3 g((unsigned)std::max(1ll, std::min<long long>(per, 4 * 152)), n_cams);
+  if (depth_f32) k_points<float><<<g, kThreads, 0, s>>>(rig, rays, fp, t, out);
+  else k_points<uint16_t><<<g, kThreads, 0, s>>>(rig, rays, fp, t, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_screen(const ScreenArgs& a, bool depth_f32, long long max_px, cudaStream_t s) {
   bool rows = true;                                   // 16-byte rows: the vector kernel
   int max_w = 1, max_h = 1;
@@ -2000,8 +2146,18 @@ cudaError_t prepare_launch(bool depth_f32) {
 cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs& fp, const Tables& t,
                          const TraceDev& tr, const OutDev& out, const Geometry& geo, cudaStream_t s,
                          cudaEvent_t* ev) {
-  if (geo.depth_f32) return launch_typed<float>(rig, rays, fp, t, tr, out, geo, s, ev);
-  return launch_typed<uint16_t>(rig, rays, fp, t, tr, out, geo, s, ev);
+  const FrameLaunch fl{rig, rays, fp, t, tr, out, &geo};
+  if (geo.depth_f32) return launch_frames<float, 1>(&fl, 1, s, ev);
+  return launch_frames<uint16_t, 1>(&fl, 1, s, ev);
+}
+
+cudaError_t launch_batch(const FrameLaunch* frames, int n, cudaStream_t s) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  for (int f = 1; f < n; ++f)                       // one depth type and one fusion variant
+    if (frames[f].geo->depth_f32 != frames[0].geo->depth_f32 || frames[f].geo->top_k != frames[0].geo->top_k)
+      return cudaErrorInvalidValue;
+  if (frames[0].geo->depth_f32) return launch_frames<float, kMaxBatch>(frames, n, s, nullptr);
+  return launch_frames<uint16_t, kMaxBatch>(frames, n, s, nullptr);
 }
 
 }  // namespace ffl

@@ -23,6 +23,7 @@ FUSEFLOW_ERR_CAPACITY = 3
 FUSEFLOW_ERR_CUDA = 4
 FUSEFLOW_ERR_TIMEOUT = 5
 FUSEFLOW_ERR_INTERNAL = 6
+FUSEFLOW_ERR_CANCELLED = 7
 FUSEFLOW_DEPTH_U16 = 0
 FUSEFLOW_DEPTH_F32 = 1
 KEY_NONE = 0xFFFFFFFFFFFFFFFF
@@ -88,6 +89,17 @@ class fuseflow_tuning(C.Structure):
                 "prefetch_tiles": self.prefetch_tiles, "programmatic": self.programmatic}
 
 
+class fuseflow_server_stats(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("rigs", C.c_int32),
+                ("slots", C.c_int32), ("inflight", C.c_int32), ("waiting", C.c_int32),
+                ("frames_submitted", C.c_int64), ("frames_completed", C.c_int64),
+                ("frames_failed", C.c_int64), ("frames_cancelled", C.c_int64),
+                ("deferred_by_budget", C.c_int64), ("slots_grown", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class fuseflow_completion(C.Structure):
     _fields_ = [("request", C.c_int64), ("rig", C.c_int32), ("status", C.c_int32),
                 ("stats", fuseflow_stats)]
@@ -104,6 +116,17 @@ EXPORTS = {
                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "fuseflow_graph_launch": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_cloud), C.c_void_p]),
     "fuseflow_graph_destroy": (None, [C.c_void_p]),
+    "fuseflow_get_cloud": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_cloud)]),
+    "fuseflow_fuse_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                       C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]),
+    "fuseflow_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "fuseflow_batch_fuse": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.c_void_p]),
+    "fuseflow_batch_graph_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p)]),
+    "fuseflow_batch_destroy": (None, [C.c_void_p]),
     "fuseflow_read_stats": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_stats), C.c_void_p]),
     "fuseflow_fuse_frame_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                            C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -152,6 +175,10 @@ EXPORTS = {
     "fuseflow_server_poll": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_completion), C.c_int32,
                                        C.POINTER(C.c_int32)]),
     "fuseflow_server_set_max_inflight": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fuseflow_server_reserve": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "fuseflow_server_remove_rig": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fuseflow_server_inject_start_failure": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "fuseflow_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(fuseflow_server_stats)]),
     "fuseflow_server_pending": (C.c_int64, [C.c_void_p]),
     "fuseflow_server_device_bytes": (C.c_int64, [C.c_void_p]),
     "fuseflow_server_destroy": (None, [C.c_void_p]),
@@ -229,7 +256,7 @@ def fuseflow_destroy(ctx) -> None:
 def _ptr_array(ptrs: Sequence[int]):
     arr = (C.c_void_p * len(ptrs))()
     for i, p in enumerate(ptrs):
-        arr[i] = int(p)
+        arr[i] = p.value if isinstance(p, C.c_void_p) else int(p)
     return arr
 
 
@@ -257,6 +284,60 @@ def fuseflow_graph_launch(graph, stream: int = 0) -> fuseflow_cloud:
 
 def fuseflow_graph_destroy(graph) -> None:
     load().fuseflow_graph_destroy(graph)
+
+
+FUSEFLOW_MAX_BATCH = 8
+
+
+def fuseflow_get_cloud(ctx) -> fuseflow_cloud:
+    cloud = fuseflow_cloud()
+    _check(load().fuseflow_get_cloud(ctx, C.byref(cloud)), "fuseflow_get_cloud")
+    return cloud
+
+
+def fuseflow_fuse_points(ctx, depth_ptrs, conf_ptrs, rgb_ptrs, pos: int, weight: int, rgb_out: int,
+                         stream: int = 0, counts: bool = True):
+    """Point-wise fusion (Table II "No SA") into caller-owned device arrays; returns
+    (n_valid, n_gated) when counts, else None (then asynchronous)."""
+    nv, ng = C.c_int64(), C.c_int64()
+    _check(load().fuseflow_fuse_points(ctx, _ptr_array(depth_ptrs), _ptr_array(conf_ptrs),
+                                       _ptr_array(rgb_ptrs), C.c_void_p(pos), C.c_void_p(weight),
+                                       C.c_void_p(rgb_out), C.byref(nv) if counts else None,
+                                       C.byref(ng) if counts else None, C.c_void_p(stream)),
+           "fuseflow_fuse_points")
+    return (nv.value, ng.value) if counts else None
+
+
+def fuseflow_batch_create(ctxs) -> C.c_void_p:
+    b = C.c_void_p()
+    _check(load().fuseflow_batch_create(_ptr_array(ctxs), len(ctxs), C.byref(b)), "fuseflow_batch_create")
+    return b
+
+
+def _nested(per_ctx):
+    """array of per-context pointer arrays (kept alive with the outer array)"""
+    inner = [_ptr_array(p) for p in per_ctx]
+    outer = (C.c_void_p * len(inner))(*[C.cast(a, C.c_void_p) for a in inner])
+    outer._keep = inner
+    return outer
+
+
+def fuseflow_batch_fuse(batch, depth_ptrs, conf_ptrs, rgb_ptrs, stream: int = 0) -> int:
+    """depth_ptrs[i] etc.: context i's per-camera device pointers; returns the status."""
+    return load().fuseflow_batch_fuse(batch, _nested(depth_ptrs), _nested(conf_ptrs),
+                                      _nested(rgb_ptrs), C.c_void_p(stream))
+
+
+def fuseflow_batch_graph_create(batch, depth_ptrs, conf_ptrs, rgb_ptrs) -> C.c_void_p:
+    g = C.c_void_p()
+    _check(load().fuseflow_batch_graph_create(batch, _nested(depth_ptrs), _nested(conf_ptrs),
+                                              _nested(rgb_ptrs), C.byref(g)),
+           "fuseflow_batch_graph_create")
+    return g
+
+
+def fuseflow_batch_destroy(batch) -> None:
+    load().fuseflow_batch_destroy(batch)
 
 
 def fuseflow_read_stats(ctx, stream: int = 0, check: bool = True):
@@ -439,6 +520,27 @@ def fuseflow_server_set_max_inflight(srv, max_inflight: int) -> None:
            "fuseflow_server_set_max_inflight")
 
 
+def fuseflow_server_reserve(srv, rig: int, n_slots: int) -> int:
+    held = C.c_int32()
+    _check(load().fuseflow_server_reserve(srv, rig, n_slots, C.byref(held)), "fuseflow_server_reserve")
+    return held.value
+
+
+def fuseflow_server_remove_rig(srv, rig: int) -> None:
+    _check(load().fuseflow_server_remove_rig(srv, rig), "fuseflow_server_remove_rig")
+
+
+def fuseflow_server_inject_start_failure(srv, n: int, status: int, after_copies: bool) -> None:
+    _check(load().fuseflow_server_inject_start_failure(srv, n, status, int(after_copies)),
+           "fuseflow_server_inject_start_failure")
+
+
+def fuseflow_server_get_stats(srv) -> dict:
+    st = fuseflow_server_stats()
+    _check(load().fuseflow_server_get_stats(srv, C.byref(st)), "fuseflow_server_get_stats")
+    return st.as_dict()
+
+
 def fuseflow_server_pending(srv) -> int:
     return int(load().fuseflow_server_pending(srv))
 
@@ -563,6 +665,69 @@ class FrameGraph:
                                        [t.data_ptr() for t in conf], [t.data_ptr() for t in rgb])
 
     def launch(self, stream: Optional[int] = None) -> fuseflow_cloud:
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_graph_launch(self.g, stream)
+
+    def close(self):
+        if self.g:
+            fuseflow_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several contexts fused by one launch of each frame kernel (fuseflow_batch_*)."""
+
+    def __init__(self, contexts: Sequence["FuseFlow"]):
+        self.contexts = list(contexts)
+        self.b = fuseflow_batch_create([c.ctx for c in self.contexts])
+
+    def fuse(self, frames, stream: Optional[int] = None) -> int:
+        """frames[i] = (depth, conf, rgb) lists of CUDA tensors of context i."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        return fuseflow_batch_fuse(self.b, *self._ptrs(frames), stream)
+
+    def fuse_ptrs(self, depth_ptrs, conf_ptrs, rgb_ptrs, stream: int) -> int:
+        return fuseflow_batch_fuse(self.b, depth_ptrs, conf_ptrs, rgb_ptrs, stream)
+
+    @staticmethod
+    def _ptrs(frames):
+        return ([[t.data_ptr() for t in f[0]] for f in frames], [[t.data_ptr() for t in f[1]] for f in frames],
+                [[t.data_ptr() for t in f[2]] for f in frames])
+
+    def graph(self, frames) -> "BatchGraph":
+        return BatchGraph(self, frames)
+
+    def close(self):
+        if self.b:
+            fuseflow_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchGraph:
+    """A recorded batch call on fixed input tensors (keep them alive while it is used)."""
+
+    def __init__(self, batch: Batch, frames):
+        self.batch = batch
+        self.frames = frames
+        self.g = fuseflow_batch_graph_create(batch.b, *Batch._ptrs(frames))
+
+    def launch(self, stream: Optional[int] = None):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

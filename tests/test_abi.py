@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol(ffmod):
 
 
 def test_status_strings(ffmod):
-    for s in range(7):
+    assert ffmod.FUSEFLOW_ERR_CANCELLED == 7
+    for s in range(8):
         assert ffmod.fuseflow_status_string(s)
     assert "unknown" in ffmod.fuseflow_status_string(99)
 
@@ -131,6 +132,11 @@ def test_server_rejects_bad_arguments_without_a_gpu(ffmod):
                                       C.byref(req)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
     assert lib.fuseflow_server_pending(None) == 0
     assert lib.fuseflow_server_device_bytes(None) == 0
+    held = C.c_int32()
+    assert lib.fuseflow_server_reserve(None, 0, 2, C.byref(held)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    assert lib.fuseflow_server_remove_rig(None, 0) == ffmod.FUSEFLOW_ERR_INVALID_ARG
+    st = ffmod.fuseflow_server_stats()
+    assert lib.fuseflow_server_get_stats(None, C.byref(st)) == ffmod.FUSEFLOW_ERR_INVALID_ARG
     lib.fuseflow_server_destroy(None)
 
 
@@ -152,6 +158,19 @@ def test_graph_entry_points_reject_bad_arguments_without_a_gpu(ffmod):
     assert lib.fuseflow_graph_create(None, None, None, None, C.byref(g)) == bad
     assert lib.fuseflow_graph_launch(None, None, None) == bad
     lib.fuseflow_graph_destroy(None)
+    # batches: counts and NULL arguments are refused before any context is touched
+    b = C.c_void_p()
+    assert lib.fuseflow_batch_create(None, 2, C.byref(b)) == bad
+    ctxs = (C.c_void_p * 9)()
+    assert lib.fuseflow_batch_create(ctxs, 0, C.byref(b)) == bad
+    assert lib.fuseflow_batch_create(ctxs, 9, C.byref(b)) == bad
+    assert lib.fuseflow_batch_create(ctxs, 2, None) == bad
+    assert lib.fuseflow_batch_fuse(None, None, None, None, None) == bad
+    assert lib.fuseflow_batch_graph_create(None, None, None, None, C.byref(g)) == bad
+    lib.fuseflow_batch_destroy(None)
+    cl = ffmod.fuseflow_cloud()
+    assert lib.fuseflow_get_cloud(None, C.byref(cl)) == bad
+    assert lib.fuseflow_fuse_points(None, None, None, None, None, None, None, None, None, None) == bad
 
 
 def test_screen_bounds_must_be_ordered_and_static_entry_has_no_screen(ffmod):
@@ -183,7 +202,8 @@ def test_struct_layouts_match_the_header(ffmod, tmp_path):
                "fuseflow_conf_params": ffmod.fuseflow_conf_params,
                "fuseflow_tuning": ffmod.fuseflow_tuning,
                "fuseflow_host_cloud": ffmod.fuseflow_host_cloud,
-               "fuseflow_completion": ffmod.fuseflow_completion}
+               "fuseflow_completion": ffmod.fuseflow_completion,
+               "fuseflow_server_stats": ffmod.fuseflow_server_stats}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fuseflow.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
