@@ -104,6 +104,17 @@ class Server:
         return [(self._done[i].request, self._done[i].rig, self._done[i].status,
                  self._done[i].stats.as_dict()) for i in range(n)]
 
+    def reserve(self, rid: int, n_slots: int) -> int:
+        """Allocates up to n_slots slots of the rig now (as the budget allows); returns the
+        number it holds."""
+        return F.fuseflow_server_reserve(self.srv, rid, n_slots)
+
+    def remove_rig(self, rid: int) -> None:
+        F.fuseflow_server_remove_rig(self.srv, rid)
+
+    def stats(self) -> dict:
+        return F.fuseflow_server_get_stats(self.srv)
+
     def set_max_inflight(self, n: int) -> None:
         """At most n frames on the device at once (0: every free slot)."""
         F.fuseflow_server_set_max_inflight(self.srv, n)
@@ -157,21 +168,40 @@ def _summary(lat_s, first_arrival, last_done, n, px_total, statuses):
             "all_ok": all(s == F.FUSEFLOW_OK for s in statuses)}
 
 
-def replay_served(server: Server, rig_ids, frames, outputs, trace, px_per_rig):
+def without_removed(trace, removals):
+    """The trace without the arrivals of each removed rig from its removal time on."""
+    cut = {r: t for t, r in removals}
+    return [(t, r) for t, r in trace if r not in cut or t < cut[r]]
+
+
+def replay_served(server: Server, rig_ids, frames, outputs, trace, px_per_rig, removals=()):
     """Replays `trace` in wall-clock time through the server.  frames[r] is rig r's pinned
-    frame, outputs[r] a deque of HostCloud buffers (at least one per slot)."""
+    frame, outputs[r] a deque of HostCloud buffers (at least one per slot).  removals:
+    (time s, rig index) events at which a rig is removed from the server (its later
+    arrivals are not submitted; frames it still had waiting are reported cancelled)."""
     with _no_gc_pauses():
-        return _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig)
+        return _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig, removals)
 
 
-def _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig):
+def _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig, removals):
     t0 = time.perf_counter()
     nxt, inflight, lat, statuses, px = 0, {}, [], [], 0
     last = t0
     first = trace[0][0] if trace else 0.0
     waiting = deque()
+    removals = sorted(removals)
+    cut = removals[0][0] if removals else None
+    removed = set()
+    n_cancelled = 0
+    arrivals = []
+    trace = without_removed(trace, removals)
     while nxt < len(trace) or inflight or waiting:
         now = time.perf_counter() - t0
+        while removals and removals[0][0] <= now:
+            _, r = removals.pop(0)
+            server.remove_rig(rig_ids[r])
+            removed.add(r)
+            waiting = deque(w for w in waiting if w[1] != r)
         while nxt < len(trace) and trace[nxt][0] <= now:
             waiting.append(trace[nxt])
             nxt += 1
@@ -188,19 +218,34 @@ def _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig):
         for req, _, status, st in server.poll():
             t_done = time.perf_counter() - t0
             t_arr, r, buf = inflight.pop(req)
+            outputs[r].append(buf)
+            if status == F.FUSEFLOW_ERR_CANCELLED:
+                n_cancelled += 1
+                continue
             lat.append(t_done - t_arr)
+            arrivals.append(t_arr)
             statuses.append(status)
             px += px_per_rig[r]
-            outputs[r].append(buf)
             last = t_done
-    return _summary(lat, first, last, len(lat), px, statuses)
+    out = _summary(lat, first, last, len(lat), px, statuses)
+    out["cancelled"] = n_cancelled
+    if cut is not None and lat:
+        la, ar = np.asarray(lat) * 1e3, np.asarray(arrivals)
+        for name, m in (("before_removal", ar < cut), ("after_removal", ar >= cut + 1.0)):
+            if m.any():
+                out[name] = {"frames": int(m.sum()), "p50_ms": round(float(np.percentile(la[m], 50)), 3),
+                             "p99_ms": round(float(np.percentile(la[m], 99)), 3)}
+        out["phases"] = "arrivals before the removal, and from 1 s after it"
+    return out
 
 
-def replay_plain(contexts, frames, outputs, trace, px_per_rig, stream: int = 0):
+def replay_plain(contexts, frames, outputs, trace, px_per_rig, stream: int = 0, removals=()):
     """The same trace through the plain path: one synchronous fuse_frame_host per frame,
-    in arrival order (a frame waits for every earlier one)."""
+    in arrival order (a frame waits for every earlier one); removed rigs' later arrivals
+    are left out as in replay_served."""
     with _no_gc_pauses():
-        return _replay_plain(contexts, frames, outputs, trace, px_per_rig, stream)
+        return _replay_plain(contexts, frames, outputs, without_removed(trace, removals),
+                             px_per_rig, stream)
 
 
 def _replay_plain(contexts, frames, outputs, trace, px_per_rig, stream):

@@ -70,17 +70,27 @@ def test_results_alone_and_in_the_mix(mods):
         srv.close()
 
 
+def _slot_bytes(SV, rig):
+    srv = SV.Server(1 << 40)
+    try:
+        srv.add_rig(rig, n_slots=1)
+        return srv.device_bytes()
+    finally:
+        srv.close()
+
+
 def test_budget_admission(mods):
     F, SV = mods
     (r1, f1), (r2, _), _ = _cases()
-    srv = SV.Server(1 << 30)
+    b1 = _slot_bytes(SV, r1)
+    srv = SV.Server(b1 + (1 << 20))
     try:
         rid = srv.add_rig(r1, n_slots=1)
         used = srv.device_bytes()
-        assert 0 < used <= 1 << 30
-        # a rig whose slots do not fit is refused and leaves nothing behind
+        assert used == b1
+        # a rig whose first slot does not fit is refused and leaves nothing behind
         status, _ = F.fuseflow_server_add_rig(srv.srv, *F.rig_arrays(r2), len(r2.cameras),
-                                              F.fuseflow_default_params(), 100000)
+                                              F.fuseflow_default_params(), 4)
         assert status == F.FUSEFLOW_ERR_CAPACITY
         assert srv.device_bytes() == used
         hc = SV.HostCloud(srv.rigs[rid]["capacity"])
@@ -183,5 +193,127 @@ def test_in_flight_cap_starts_frames_in_submission_order(mods):
             _same(hc.cells(st["n_cells"]), alone[r]["cells"])
         with pytest.raises(F.FuseFlowError):
             srv.set_max_inflight(-1)
+    finally:
+        srv.close()
+
+
+def _submit_all(SV, srv, rid, pinned, n):
+    bufs = {}
+    for k in range(n):
+        hc = SV.HostCloud(srv.rigs[rid]["capacity"])
+        bufs[srv.submit(rid, pinned[k % len(pinned)], hc)] = (k % len(pinned), hc)
+    return bufs
+
+
+def test_a_binding_budget_limits_the_slots_and_frames_wait_for_memory(mods):
+    """A rig asking for 4 frames in flight under a budget of 2.5 slots holds 2 after
+    reserving; of six frames submitted at once the ones that find both busy wait (deferred
+    by the budget), and every result is the one the frame gives alone."""
+    F, SV = mods
+    r2 = S.tiny_rig(n=3, width=96, height=64, spread_deg=25.0)
+    frs = [S.random_frame(r2, seed=40 + k) for k in range(3)]
+    alone = [_alone(F, r2, f) for f in frs]
+    b = _slot_bytes(SV, r2)
+    srv = SV.Server(int(2.5 * b))
+    try:
+        rid = srv.add_rig(r2, n_slots=4)
+        assert srv.stats()["slots"] == 1
+        assert srv.reserve(rid, 4) == 2
+        pinned = [SV.pinned_frame(f) for f in frs]
+        bufs = _submit_all(SV, srv, rid, pinned, 6)
+        done = srv.drain()
+        st = srv.stats()
+        assert st["slots"] == 2 and st["used_bytes"] == 2 * b <= st["budget_bytes"]
+        assert st["deferred_by_budget"] >= 1 and st["frames_completed"] == 6
+        for req, _, status, s_ in done:
+            k, hc = bufs[req]
+            assert status == F.FUSEFLOW_OK
+            _same(hc.cells(s_["n_cells"]), alone[k]["cells"])
+    finally:
+        srv.close()
+
+
+def test_a_removed_rigs_memory_goes_to_rigs_below_their_request(mods):
+    F, SV = mods
+    r2 = S.tiny_rig(n=3, width=96, height=64, spread_deg=25.0)
+    fr = S.random_frame(r2, seed=44)
+    alone = _alone(F, r2, fr)
+    b = _slot_bytes(SV, r2)
+    srv = SV.Server(3 * b + (1 << 20))
+    try:
+        a = srv.add_rig(r2, n_slots=1)
+        c = srv.add_rig(r2, n_slots=3)
+        assert srv.reserve(c, 3) == 2                 # the budget is full: 3 slots
+        srv.remove_rig(a)
+        st = srv.stats()
+        assert st["rigs"] == 1 and st["slots"] == 3 and st["used_bytes"] == 3 * b
+        pinned = [SV.pinned_frame(fr)]
+        bufs = _submit_all(SV, srv, c, pinned, 3)     # all three start at once
+        assert srv.stats()["inflight"] == 3
+        for req, rig, status, s_ in srv.drain():
+            assert rig == c and status == F.FUSEFLOW_OK
+            _same(bufs[req][1].cells(s_["n_cells"]), alone["cells"])
+    finally:
+        srv.close()
+
+
+def test_removing_a_rig_finishes_its_frames_cancels_the_waiting_ones_and_frees_memory(mods):
+    F, SV = mods
+    (r1, f1), (r2, f2), _ = _cases()
+    alone = _alone(F, r1, f1)
+    srv = SV.Server(4 << 30)
+    try:
+        a = srv.add_rig(r1, n_slots=1)
+        c = srv.add_rig(r2, n_slots=1)
+        used_c = _slot_bytes(SV, r2)
+        pa = [SV.pinned_frame(f1)]
+        bufs = _submit_all(SV, srv, a, pa, 3)       # one on the slot, two waiting
+        srv.remove_rig(a)
+        assert srv.device_bytes() == used_c
+        done = srv.drain()
+        assert sorted(d[0] for d in done) == sorted(bufs)
+        status = {req: st_ for req, _, st_, _ in done}
+        first = min(bufs)
+        assert status[first] == F.FUSEFLOW_OK
+        _same(bufs[first][1].cells(next(d[3] for d in done if d[0] == first)["n_cells"]), alone["cells"])
+        assert all(status[r] == F.FUSEFLOW_ERR_CANCELLED for r in bufs if r != first)
+        st = srv.stats()
+        assert st["rigs"] == 1 and st["frames_cancelled"] == 2
+        with pytest.raises(F.FuseFlowError):
+            srv.submit(a, pa[0], SV.HostCloud(16))
+        pc = SV.pinned_frame(f2)                    # the remaining rig still serves
+        srv.submit(c, pc, SV.HostCloud(srv.rigs[c]["capacity"]))
+        (_, rig, st_, _), = srv.drain()
+        assert rig == c and st_ == F.FUSEFLOW_OK
+    finally:
+        srv.close()
+
+
+@pytest.mark.parametrize("after_copies", [False, True])
+def test_a_frame_whose_start_fails_is_reported_with_its_error(mods, after_copies):
+    """A start that fails (made on the host with the server's injection hook, before or after
+    the frame's image copies were queued) is reported by poll with its request id and the
+    error, the latter only once its copies are done; the next frame runs normally."""
+    F, SV = mods
+    r1, _, f1 = S.config1()
+    alone = _alone(F, r1, f1)
+    srv = SV.Server(1 << 30)
+    try:
+        rid = srv.add_rig(r1, n_slots=1)
+        pf = SV.pinned_frame(f1)
+        cap = srv.rigs[rid]["capacity"]
+        F.fuseflow_server_inject_start_failure(srv.srv, 1, F.FUSEFLOW_ERR_CUDA, after_copies)
+        bad, good = SV.HostCloud(cap), SV.HostCloud(cap)
+        req = srv.submit(rid, pf, bad)
+        req2 = srv.submit(rid, pf, good)
+        done = {d[0]: d for d in srv.drain()}
+        assert set(done) == {req, req2}
+        assert done[req][2] == F.FUSEFLOW_ERR_CUDA
+        assert done[req2][2] == F.FUSEFLOW_OK
+        _same(good.cells(done[req2][3]["n_cells"]), alone["cells"])
+        st = srv.stats()
+        assert st["frames_failed"] == 1 and st["frames_completed"] == 1 and srv.pending() == 0
+        with pytest.raises(F.FuseFlowError):
+            F.fuseflow_server_inject_start_failure(srv.srv, 1, F.FUSEFLOW_OK, False)
     finally:
         srv.close()
