@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "depth px/s and frames/s at 8x1280x720 views; p50/p99 latency, served vs plain"
 KERNELS_PER_FRAME = 6      # count, levels, assign, reduce, scan, emit
 CELL_OUT_BYTES = 44        # pos 12 + rgb 12 + weight 4 + count 4 + rep 4 + key 8
+SERVE_MAX_SLOTS = 4        # frames of one served rig in flight at most (slots asked per rig)
 
 
 def parse():
@@ -46,6 +47,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival trace of the served/plain comparison")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-slots", type=int, default=SERVE_MAX_SLOTS,
+                    help="frames of one served rig in flight at most (slots asked per rig)")
     ap.add_argument("--serve-max-inflight", type=int, default=0,
                     help="frames on the device at once in the served replay (0: every free slot)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -555,6 +558,7 @@ def run_ours(args, rank, world, local_rank):
     cap = ff.capacity
     srv = SV.Server(1 << 40)
     rid = srv.add_rig(rig, n_slots=B)
+    srv.reserve(rid, B)
     if not args.no_autotune:
         srv.autotune(rid, pinned[0], reps=9)
     outs = deque(SV.HostCloud(cap) for _ in range(B + 1))
@@ -588,8 +592,11 @@ def run_ours(args, rank, world, local_rank):
     # the synchronous single-call host entry point, for reference
     ctx_host = [SV.HostCloud(cap)]
     h = ctx_host[0].c
+    fr0 = pinned[0]                               # untimed: the staging buffers' first use
+    F.fuseflow_fuse_frame_host(ff.ctx, fr0["depth"], fr0["conf"], fr0["rgb"], h.pos, h.rgb,
+                               h.weight, h.count, h.rep, h.key, sh)
     t0 = time.perf_counter()
-    n_single = min(16, n_e2e)
+    n_single = min(64, n_e2e)
     for i in range(n_single):
         fr = pinned[i % len(pinned)]
         F.fuseflow_fuse_frame_host(ff.ctx, fr["depth"], fr["conf"], fr["rgb"], h.pos, h.rgb,
@@ -945,7 +952,6 @@ def run_ablations(dev, rig, frames, frames_each: int = 64):
 
 # ----------------------------------------------------------------------------- serving
 SERVE_BUDGET = 40 << 30          # HBM budget of the served rigs' slots (bytes)
-SERVE_MAX_SLOTS = 4              # frames of one rig in flight at most (slots grow on demand)
 
 
 def serving_child(arg_dict, local_rank, out_queue):
@@ -992,12 +998,12 @@ def run_serving(args, dev):
 
     def served_run(trace_, removals_):
         srv = SV.Server(SERVE_BUDGET)
-        rids = [srv.add_rig(rig, n_slots=SERVE_MAX_SLOTS, max_cells=caps[r]) for r, rig in enumerate(rigs)]
-        for k in range(2, SERVE_MAX_SLOTS + 1):          # share the budget evenly, round-robin
+        rids = [srv.add_rig(rig, n_slots=args.serve_slots, max_cells=caps[r]) for r, rig in enumerate(rigs)]
+        for k in range(2, args.serve_slots + 1):         # share the budget evenly, round-robin
             held = [srv.reserve(rid, k) for rid in rids]
         srv.set_max_inflight(args.serve_max_inflight)
         from collections import deque
-        outs = [deque(SV.HostCloud(caps[r]) for _ in range(SERVE_MAX_SLOTS + 1)) for r in range(n)]
+        outs = [deque(SV.HostCloud(caps[r]) for _ in range(args.serve_slots + 1)) for r in range(n)]
         for r in range(n):                           # warm-up: one frame per rig
             buf = outs[r].popleft()
             srv.submit(rids[r], pinned[r], buf)
@@ -1007,7 +1013,7 @@ def run_serving(args, dev):
         res = SV.replay_served(srv, rids, pinned, outs, trace_, px, removals=removals_)
         after = srv.stats()
         srv.close()
-        res["admission"] = {"budget_bytes": SERVE_BUDGET, "slots_asked_per_rig": SERVE_MAX_SLOTS,
+        res["admission"] = {"budget_bytes": SERVE_BUDGET, "slots_asked_per_rig": args.serve_slots,
                             "slots_held_per_rig": held, "hbm_bytes_at_start": int(before["used_bytes"]),
                             "hbm_bytes_at_end": int(after["used_bytes"]),
                             "slots_at_end": int(after["slots"]),

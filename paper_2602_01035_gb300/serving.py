@@ -236,6 +236,12 @@ def _replay_served(server, rig_ids, frames, outputs, trace, px_per_rig, removals
                 out[name] = {"frames": int(m.sum()), "p50_ms": round(float(np.percentile(la[m], 50)), 3),
                              "p99_ms": round(float(np.percentile(la[m], 99)), 3)}
         out["phases"] = "arrivals before the removal, and from 1 s after it"
+    if lat:
+        la, ar = np.asarray(lat) * 1e3, np.asarray(arrivals)
+        w = 10.0
+        out["p99_ms_per_10s"] = [round(float(np.percentile(la[(ar >= t) & (ar < t + w)], 99)), 2)
+                                 for t in np.arange(0.0, float(ar.max()) + 1e-9, w)
+                                 if ((ar >= t) & (ar < t + w)).any()]
     return out
 
 
