@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "depth px/s and frames/s at 8x1280x720 views; p50/p99 latency, served vs plain"
 KERNELS_PER_FRAME = 6      # count, levels, assign, reduce, scan, emit
 CELL_OUT_BYTES = 44        # pos 12 + rgb 12 + weight 4 + count 4 + rep 4 + key 8
-SERVE_MAX_SLOTS = 4        # frames of one served rig in flight at most (slots asked per rig)
+SERVE_MAX_SLOTS = 2        # frames of one served rig in flight at most (slots asked per rig)
 
 
 def parse():
@@ -951,14 +951,18 @@ def run_ablations(dev, rig, frames, frames_each: int = 64):
 
 
 # ----------------------------------------------------------------------------- serving
-SERVE_BUDGET = 40 << 30          # HBM budget of the served rigs' slots (bytes)
+SERVE_BUDGET = 20 << 30          # HBM budget of the served rigs' slots (bytes): binds below
+                                 # the 24 slots the 12 rigs ask for
 
 
 def serving_child(arg_dict, local_rank, out_queue):
     """run_serving in a process of its own (module level, for a spawn context).  The server
-    gives each of its 24 slots a stream; with CUDA's default 8 hardware work queues, streams
+    gives each of its slots a stream; with CUDA's default 8 hardware work queues, streams
     that share a queue serialise, which lengthened the latency tail, so this process asks
-    for 32 before it initialises CUDA."""
+    for 32 before it initialises CUDA.  The rigs ask for 24 slots in all, under the 32:
+    with 36 to 43 slots (3 or 4 per rig) the served p99 of a 30 s trace grew from 5 ms to
+    68-140 ms, growing window by window, as frames of different rigs queued behind one
+    another in shared queues."""
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     torch.cuda.set_device(local_rank)
@@ -999,6 +1003,7 @@ def run_serving(args, dev):
     def served_run(trace_, removals_):
         srv = SV.Server(SERVE_BUDGET)
         rids = [srv.add_rig(rig, n_slots=args.serve_slots, max_cells=caps[r]) for r, rig in enumerate(rigs)]
+        held = [1] * n
         for k in range(2, args.serve_slots + 1):         # share the budget evenly, round-robin
             held = [srv.reserve(rid, k) for rid in rids]
         srv.set_max_inflight(args.serve_max_inflight)
