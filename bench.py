@@ -229,7 +229,8 @@ def run_ours(args, rank, world, local_rank):
     FPS = args.frames_per_step
 
     # launch geometry: the autotuner's choice on the pool's first frame (untimed set-up);
-    # results do not depend on it, so every context of this rig takes the same setting
+    # every context of this rig takes the same setting (the tile height moves fused values
+    # in their last bits only, and a batch needs one tile height)
     tuning = {"autotuned": False, "chosen": ff.tuning()}
     if not args.no_autotune:
         d0 = dtensors[0]
@@ -241,7 +242,8 @@ def run_ours(args, rank, world, local_rank):
 
     def tuned(ctx_obj):
         g = tuning["chosen"]
-        ctx_obj.set_tuning(g["count_chunks"], g["emit_blocks"], g["prefetch_tiles"], g["programmatic"])
+        ctx_obj.set_tuning(g["count_chunks"], g["emit_blocks"], g["prefetch_tiles"], g["programmatic"],
+                           g["tile_h"])
         return ctx_obj
 
     def step():
@@ -315,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
         ctxs = [ff] + [tuned(F.FuseFlow(rig)) for _ in range(B - 1)]
         g_ = tuning["chosen"]
         for c_ in ctxs:
-            c_.set_tuning(g_["count_chunks"], g_["emit_blocks"], g_["prefetch_tiles"], 0)
+            c_.set_tuning(g_["count_chunks"], g_["emit_blocks"], g_["prefetch_tiles"], 0, g_["tile_h"])
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(B - 1)]
 
         def batched_step():
@@ -689,7 +691,7 @@ def run_batched_launch(F, torch, dev, stream, rig, dtensors, tuning, FPS, steps,
     pdl = g_["programmatic"] if n_streams == 1 else 0
     ctxs = [F.FuseFlow(rig) for _ in range(B * n_streams)]
     for c in ctxs:
-        c.set_tuning(g_["count_chunks"], g_["emit_blocks"], g_["prefetch_tiles"], pdl)
+        c.set_tuning(g_["count_chunks"], g_["emit_blocks"], g_["prefetch_tiles"], pdl, g_["tile_h"])
     batches = [F.Batch(ctxs[k * B:(k + 1) * B]) for k in range(n_streams)]
     streams = [stream] + [torch.cuda.Stream(dev) for _ in range(n_streams - 1)]
     n_groups = max(1, len(dtensors) // B)
@@ -777,6 +779,12 @@ def run_mixed_batch(F, torch, dev, groups, reps=64):
     ctxs = [F.FuseFlow(rig) for rig in rigs]
     for c, t in zip(ctxs, dev_frames):
         c.autotune(t[0], t[1], t[2], reps=9, stream=sh)
+    # one assign kernel serves the batch: every context takes the tile height chosen for the
+    # rig with the most pixels
+    th = ctxs[max(range(len(ctxs)), key=lambda i: ctxs[i].n_pixels)].tuning()["tile_h"]
+    for c in ctxs:
+        tu_ = c.tuning()
+        c.set_tuning(tu_["count_chunks"], tu_["emit_blocks"], tu_["prefetch_tiles"], tu_["programmatic"], th)
     batch = F.Batch(ctxs)
     g = batch.graph(dev_frames)
     plain = [c.graph(*t) for c, t in zip(ctxs, dev_frames)]

@@ -189,8 +189,10 @@ int fuseflow_get_cloud(const fuseflow_ctx *ctx, fuseflow_cloud *out);
  * batch call runs; the batch holds pointers to them and does not own them.
  * fuseflow_batch_graph_create records one batch call on fixed input buffers as a CUDA
  * graph (replayed with fuseflow_graph_launch, whose cloud argument receives context 0's).
+ * The contexts' tile heights (fuseflow_tuning.tile_h) must agree when a batch call is
+ * made or recorded: one assign kernel serves the whole batch.
  * Returns INVALID_ARG (count, mixed formats or variants, a screen, a repeated context,
- * NULL pointers), OUT_OF_MEMORY, CUDA. */
+ * NULL pointers, tile heights that differ at call time), OUT_OF_MEMORY, CUDA. */
 #define FUSEFLOW_MAX_BATCH 8
 typedef struct fuseflow_batch fuseflow_batch;
 int fuseflow_batch_create(fuseflow_ctx *const *ctxs, int32_t n, fuseflow_batch **out);
@@ -293,8 +295,13 @@ int fuseflow_read_stage_times(fuseflow_ctx *ctx, double *ms, int64_t *n_frames);
 const char *fuseflow_stage_name(int stage);
 
 /* Launch geometry of a context: performance knobs only.  The fused cloud, its statistics
- * and any trace are bitwise the same for every admissible setting (the path has no
- * order-dependent arithmetic), so a setting can be chosen by timing alone.
+ * and any trace are bitwise the same for every admissible setting of the first four (the
+ * path has no order-dependent arithmetic); tile_h changes how each cell's members are
+ * grouped into per-tile fixed-point partial sums, so keys, counts, representatives, the
+ * trace and the statistics stay bitwise the same while weights, positions and colours
+ * may move in their last bits (far inside the 1e-5 relative tolerance: each partial is
+ * exact at a scale of 2^-36 of the largest weight in its tile, and shifting it to the
+ * cell's scale truncates below that).  A setting can be chosen by timing alone.
  *   count_chunks    2048-pixel chunks per block of the coarse-count step, 1..64
  *   emit_blocks     blocks of the level, reduce and emit steps, 1..65536
  *   prefetch_tiles  how many assign tiles ahead each assign block prefetches its
@@ -305,14 +312,18 @@ const char *fuseflow_stage_name(int stage);
  *                   device); 1: the same except between the assign and reduce steps (early
  *                   reduce blocks slow the assign step's last wave on large frames); 0:
  *                   plain stream order.  Stage timing always uses plain order.
+ *   tile_h          rows of the assign step's tiles of 32 columns: 8 (128 threads a
+ *                   block), 16 (256) or 32 (512); 0 in fuseflow_set_tuning keeps the
+ *                   current height
  * fuseflow_create picks count_chunks for one wave of four count blocks per SM (at most 6),
- * emit_blocks = 8 blocks per SM, prefetch_tiles = one wave of assign blocks, and
- * programmatic = 2 for rigs of fewer than 2^21 pixels, 1 otherwise. */
+ * emit_blocks = 8 blocks per SM, prefetch_tiles = one wave of assign blocks,
+ * programmatic = 2 for rigs of fewer than 2^21 pixels, 1 otherwise, and tile_h = 16. */
 typedef struct fuseflow_tuning {
   int32_t count_chunks;
   int32_t emit_blocks;
   int32_t prefetch_tiles;
   int32_t programmatic;       /* 0, 1 or 2 */
+  int32_t tile_h;             /* 8, 16 or 32 (0: keep, in set) */
 } fuseflow_tuning;
 
 /* Reads (get) or replaces (set) the context's launch geometry.  set returns INVALID_ARG,
@@ -324,8 +335,8 @@ int fuseflow_set_tuning(fuseflow_ctx *ctx, const fuseflow_tuning *in);
 
 /* Autotuner of the launch geometry.  Fuses the given frame (DEVICE inputs as for
  * fuseflow_fuse_frame) repeatedly on `stream` under candidate settings, one knob at a
- * time (count_chunks, emit_blocks, prefetch_tiles, then programmatic; coordinate descent from
- * the context's current setting), and keeps a candidate only when the median of `reps`
+ * time (tile_h, count_chunks, emit_blocks, prefetch_tiles, then programmatic; coordinate
+ * descent from the context's current setting), and keeps a candidate only when the median of `reps`
  * timed frames (CUDA events on `stream`, L2 flushed before each frame by writing a
  * scratch buffer of twice the L2 size) is at least 1 % below the best so far.  The
  * chosen setting stays in the context and is copied to *chosen (may be NULL);

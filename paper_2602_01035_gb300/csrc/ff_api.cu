@@ -417,8 +417,8 @@ int fuseflow_create(const fuseflow_intrinsics* intr, const fuseflow_extrinsics* 
   const size_t q_key = take_out(sizeof(unsigned long long) * (size_t)ctx->max_cells);
   ctx->out_bytes = po;
 
-  const int n_tiles = fill_tile_index(*rig, &ctx->geo.tiles);
-  ctx->geo.tiles.ahead = assign_resident_blocks() * sms;
+  const int n_tiles = fill_tile_index(*rig, &ctx->geo.tiles, 16);
+  ctx->geo.tiles.ahead = assign_resident_blocks(16, rig->k1) * sms;
   std::vector<BlockConst> bconst((size_t)n_cams);
   fill_block_consts(*rig, bconst.data());
   const size_t pray_at = align_up(sizeof(BlockConst) * (size_t)n_cams, 256);
@@ -616,6 +616,8 @@ static int batch_frames(const fuseflow_batch* b, const void* const* const* depth
   if (!b || !depth || !conf || !rgb) return FUSEFLOW_ERR_INVALID_ARG;
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     const fuseflow_ctx* c = b->ctx[i];
+    // one assign kernel serves the batch: its contexts share the tile height at call time
+    if (c->geo.tiles.th != b->ctx[0]->geo.tiles.th) return FUSEFLOW_ERR_INVALID_ARG;
     int ok = 0;
     fl[i].fp = frame_ptrs(c, depth[i], conf[i], rgb[i], &ok);
     if (!ok) return FUSEFLOW_ERR_INVALID_ARG;
@@ -937,6 +939,7 @@ static void apply_tuning(fuseflow_ctx* ctx, const fuseflow_tuning& tu) {
   ctx->geo.emit_blocks = tu.emit_blocks;
   ctx->geo.tiles.ahead = tu.prefetch_tiles == 0 ? kNoPrefetch : std::min(tu.prefetch_tiles, kNoPrefetch);
   ctx->geo.pdl = tu.programmatic;
+  if (tu.tile_h != 0 && tu.tile_h != ctx->geo.tiles.th) ctx->tab.n_tiles = retile(&ctx->geo.tiles, tu.tile_h);
 }
 
 // Coordinate descent over the launch geometry, timing whole frames on one stream.
@@ -982,6 +985,8 @@ struct Autotuner {
 
   int run() {
     int dev = 0, l2 = 0, sms = 0;
+    // the tile height goes first: it moves the assign step most, and the prefetch distance
+    // below counts its tiles
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1008,6 +1013,15 @@ struct Autotuner {
       if (r == FUSEFLOW_OK && us < 0.99 * best_us) { best = cand; best_us = us; }
       return r;
     };
+    for (int h : {8, 16, 32}) {
+      fuseflow_tuning c = best;
+      c.tile_h = h;
+      if (h != best.tile_h) {          // the prefetch distance scaled to the same wave of pixels
+        const long long a = best.prefetch_tiles;
+        c.prefetch_tiles = (int)std::min<long long>(kNoPrefetch - 1, a * best.tile_h / h);
+      }
+      if ((st = consider(c)) != FUSEFLOW_OK) return st;
+    }
     // count_chunks: one wave of b count blocks per SM, for b in 1..8
     long long total_chunks = 0;
     for (int i = 0; i < ctx->n_cams; ++i)
@@ -1027,7 +1041,7 @@ struct Autotuner {
       c.emit_blocks = b * sms;
       if ((st = consider(c)) != FUSEFLOW_OK) return st;
     }
-    const int wave = assign_resident_blocks() * sms;
+    const int wave = assign_resident_blocks(best.tile_h, ctx->k1) * sms;
     for (int a : {0, wave / 2, wave, 2 * wave}) {
       fuseflow_tuning c = best;
       c.prefetch_tiles = a;
@@ -1055,12 +1069,14 @@ int fuseflow_get_tuning(const fuseflow_ctx* ctx, fuseflow_tuning* out) {
   out->emit_blocks = ctx->geo.emit_blocks;
   out->prefetch_tiles = ctx->geo.tiles.ahead >= kNoPrefetch ? 0 : ctx->geo.tiles.ahead;
   out->programmatic = ctx->geo.pdl;
+  out->tile_h = ctx->geo.tiles.th;
   return FUSEFLOW_OK;
 }
 
 int fuseflow_set_tuning(fuseflow_ctx* ctx, const fuseflow_tuning* in) {
   if (!ctx || !in || in->count_chunks < 1 || in->count_chunks > 64 || in->emit_blocks < 1 ||
-      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || in->programmatic < 0 || in->programmatic > 2)
+      in->emit_blocks > 65536 || in->prefetch_tiles < 0 || in->programmatic < 0 || in->programmatic > 2 ||
+      (in->tile_h != 0 && in->tile_h != 8 && in->tile_h != 16 && in->tile_h != 32))
     return FUSEFLOW_ERR_INVALID_ARG;
   apply_tuning(ctx, *in);
   return FUSEFLOW_OK;
@@ -1276,11 +1292,11 @@ extern "C" int fuseflow_fuse_frame_static(const fuseflow_intrinsics* intr,
   const int nr = (int)n_rays;
   const int np = (int)(2ll * k1 * n_rays);
   Geometry geo{};
-  const int n_tiles = fill_tile_index(rig, &geo.tiles);
+  const int n_tiles = fill_tile_index(rig, &geo.tiles, 16);
   {
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-    geo.tiles.ahead = assign_resident_blocks() * sm_count;
+    geo.tiles.ahead = assign_resident_blocks(16, rig.k1) * sm_count;
   }
   fill_block_consts(rig, g_static_bconst);
   // pageable host -> device copies return once the host buffers have been read

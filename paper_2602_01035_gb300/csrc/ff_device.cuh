@@ -80,9 +80,10 @@ struct BlockConst {
 };
 
 // Where the assign step's tiles are: camera i owns tiles [first[i], first[i+1]), row-major
-// over its ceil(W/32) x ceil(H/16) grid.  Passed by value (constant bank) to the kernel.
+// over its ceil(W/32) x ceil(H/th) grid.  Passed by value (constant bank) to the kernel.
 struct TileIndex {
   int n_cams, k1;
+  int th;                        // tile height (8, 16 or 32 rows of 32 columns)
   int first[kMaxCams + 1];
   int W[kMaxCams], H[kMaxCams];
   long long off[kMaxCams];       // global index of each camera's pixel (0, 0)

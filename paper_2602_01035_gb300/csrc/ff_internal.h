@@ -185,8 +185,12 @@ struct ConfArgs {
 cudaError_t launch_confidence(const ConfArgs& a, bool depth_f32, int max_w, int max_h,
                               cudaStream_t s);
 
-int assign_resident_blocks();          // assign-step blocks resident per SM (launch bounds)
-int fill_tile_index(const RigDev& rig, TileIndex* out);
+// assign-step blocks resident per SM for tiles of th rows and k1 neighbour views
+int assign_resident_blocks(int th, int k1);
+// tiles of th rows (8, 16 or 32) of the rig's cameras; returns their number
+int fill_tile_index(const RigDev& rig, TileIndex* out, int th);
+// the same index re-cut into tiles of th rows; returns their number
+int retile(TileIndex* ti, int th);
 void fill_block_consts(const RigDev& rig, BlockConst* out);
 // Kernel attributes a frame's launches need (called by context creation, so that a later
 // stream capture of launch_frame makes no attribute call).

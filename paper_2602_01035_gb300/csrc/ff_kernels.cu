@@ -40,9 +40,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kCountPx = 8;                       // pixels per thread in the count step
 constexpr int kCountBlockPx = kThreads * kCountPx;
-constexpr int kTileW = 32, kTileH = 16;           // assign/accum tile: one warp per 2 rows
-constexpr int kTilePx = kTileW * kTileH;
-constexpr int kPrayPerView = 2 * kTileW + 2 * kTileH;   // staged pair-ray float4 per view
+constexpr int kTileW = 32;                        // assign tile: 32 columns by TH rows
 constexpr int kMaxProbe = 1 << 14;
 constexpr float kLn2H = 0.693147182464599609375f;         // float(ln 2)
 constexpr float kLn2L = -1.904654299957768e-09f;          // ln 2 - kLn2H
@@ -148,7 +146,7 @@ template <int TS, typename K>
 __device__ __forceinline__ int local_pos(K* tab, K empty, K key, int max_probe, bool& fresh) {
   unsigned h;
   if constexpr (sizeof(K) == 4) {
-    constexpr int kBits = TS == 1024 ? 10 : TS == 2048 ? 11 : TS == 4096 ? 12 : 0;
+    constexpr int kBits = TS == 512 ? 9 : TS == 1024 ? 10 : TS == 2048 ? 11 : TS == 4096 ? 12 : 0;
     static_assert(kBits > 0, "block table size");
     h = ((unsigned)key * 0x9E3779B1u) >> (32 - kBits);
   } else {
@@ -200,17 +198,19 @@ __device__ __forceinline__ int exact_round(float fh, float fl, float ch, float c
 // groups spill at four blocks per SM and grow the code past the instruction cache).
 constexpr int kViewGroup = 1;
 
-// Pair rays of a tile staged in shared memory (pixel (lx, ly) of the tile).
+// Pair rays of a tile of TH rows staged in shared memory (pixel (lx, ly) of the tile): per
+// view, A of the 32 columns and B of the TH rows, each as two float4 planes.
+template <int TH>
 struct TilePairRays {
   const float4* s_pr;
   int lx, ly;
   __device__ __forceinline__ void operator()(int q, const PairDev&, float4& a01, float4& a2,
                                              float4& b01, float4& b2) const {
-    const float4* pr = s_pr + q * kPrayPerView;
+    const float4* pr = s_pr + q * (2 * kTileW + 2 * TH);
     a01 = pr[lx];
     a2 = pr[kTileW + lx];
     b01 = pr[2 * kTileW + ly];
-    b2 = pr[2 * kTileW + kTileH + ly];
+    b2 = pr[2 * kTileW + TH + ly];
   }
 };
 
@@ -596,44 +596,53 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
 }
 
 // ------------------------------------------------------------------ assign step
-constexpr int kAssignTS = 2 * kTilePx;     // shared hash positions (keys <= pixels of a tile)
-// Distinct cells of a tile with shared-memory accumulators.  In a tile with more distinct
-// cells (sparse, noisy tiles only) the cells with two or more members in the tile take the
-// accumulators and every other member files a single-member partial, which is the record
-// the accumulator would have produced for it; if even the multi-member cells are too many,
-// every member files alone.  Both rules depend on the tile's cells alone, never on the
-// order of the insertions, so that every cell's sums, and the fused cloud, are bitwise
-// reproducible.
-constexpr int kAssignNL = kTilePx / 2;
-static_assert(kMaxTopK * 8 <= 14 * 4, "a cell's top-k keys fit in its 14 split-sum words");
-constexpr int kAssignThreads = 16 * kTileH;        // one warp per two rows of the tile
-constexpr int kAssignWarps = kAssignThreads / 32;
-// registers (64 a thread) and shared memory allow this many blocks of a 32x16 tile
-constexpr int kAssignBlocksPerSM = 4 * 256 / kAssignThreads;
-constexpr int kConstWords = (int)((sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev))) / 4 +
-                                  kAssignThreads - 1) / kAssignThreads;
 constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
-static_assert(kConstWords <= 4, "a few words per thread copy a block's constants");
-constexpr size_t kSmBC = 0;
-// per hash position (kAssignTS): cell slot, entry index, smallest weight exponent, largest
-// ordered C, member count; the last four are contiguous so that one loop clears them
-constexpr size_t kSmFK = align16(kSmBC + sizeof(BlockConst));      // u32 cell slot
-constexpr size_t kSmMinP = kSmFK + 4 * kAssignTS;                  // int smallest exponent
-constexpr size_t kSmCmaxP = kSmMinP + 4 * kAssignTS;               // u32 largest ordered C
-constexpr size_t kSmCntP = kSmCmaxP + 4 * kAssignTS;               // u32 members
-constexpr size_t kSmFI = align16(kSmCntP + 4 * kAssignTS);         // int entry of a position
-// per entry (kAssignNL): key, hash position, lowest index at the largest C, split sums
-constexpr size_t kSmEK = align16(kSmFI + 4 * kAssignTS);           // u64 key
-constexpr size_t kSmEP = align16(kSmEK + 8 * kAssignNL);           // u32 hash position
-constexpr size_t kSmGmin = align16(kSmEP + 4 * kAssignNL);         // u32 lowest index
-constexpr size_t kSmAcc = align16(kSmGmin + 4 * kAssignNL);        // u32[14][NL] split sums
-constexpr size_t kSmPid = align16(kSmAcc + 14 * 4 * kAssignNL);    // u16[tile] gated pixels
-constexpr size_t kSmZ = align16(kSmPid + 2 * kTilePx);             // f32[tile] their depth
-constexpr size_t kSmC = align16(kSmZ + 4 * kTilePx);               // f32[tile] confidence
-constexpr size_t kSmRGB = align16(kSmC + 4 * kTilePx);             // u32[tile] colour
-constexpr size_t kSmPR = align16(kSmRGB + 4 * kTilePx);            // float4[K1][96] pair rays
-// dynamic shared memory of a launch with k1 neighbour views
-constexpr size_t assign_smem(int k1) { return kSmPR + 16 * (size_t)k1 * kPrayPerView; }
+static_assert(kMaxTopK * 8 <= 14 * 4, "a cell's top-k keys fit in its 14 split-sum words");
+
+// The assign step's tile: 32 columns by TH rows (TH = 8, 16 or 32: a launch-geometry
+// choice), one warp per two rows, two pixels a thread, and its shared-memory layout.
+// Distinct cells of a tile with shared-memory accumulators: NL.  In a tile with more
+// distinct cells (sparse, noisy tiles only) the cells with two or more members in the tile
+// take the accumulators and every other member files a single-member partial, which is the
+// record the accumulator would have produced for it; if even the multi-member cells are too
+// many, every member files alone.  Both rules depend on the tile's cells alone, never on
+// the order of the insertions, so that every cell's sums, and the fused cloud, are bitwise
+// reproducible for a given tile shape.
+template <int TH>
+struct AssignTile {
+  static_assert(TH == 8 || TH == 16 || TH == 32, "tile heights");
+  static constexpr int Px = kTileW * TH;
+  static constexpr int Threads = 16 * TH;
+  static constexpr int Warps = Threads / 32;
+  // registers (64 a thread) allow this many blocks per SM (shared memory may allow fewer)
+  static constexpr int BlocksPerSM = 4 * 256 / Threads;
+  static constexpr int PrayPerView = 2 * kTileW + 2 * TH;  // staged pair-ray float4 per view
+  static constexpr int TS = 2 * Px;                         // shared hash positions
+  static constexpr int NL = Px / 2;                         // accumulator entries
+  static constexpr int ConstWords =
+      (int)((sizeof(CamDev) + kMaxK1 * (sizeof(PairDev) + sizeof(CamDev))) / 4 + Threads - 1) / Threads;
+  static_assert(ConstWords <= 4, "a few words per thread copy a block's constants");
+  static constexpr size_t BC = 0;
+  // per hash position (TS): cell slot, entry index, smallest weight exponent, largest
+  // ordered C, member count; the last four are contiguous so that one loop clears them
+  static constexpr size_t FK = align16(BC + sizeof(BlockConst));   // u32 cell slot
+  static constexpr size_t MinP = FK + 4 * TS;                      // int smallest exponent
+  static constexpr size_t CmaxP = MinP + 4 * TS;                   // u32 largest ordered C
+  static constexpr size_t CntP = CmaxP + 4 * TS;                   // u32 members
+  static constexpr size_t FI = align16(CntP + 4 * TS);             // int entry of a position
+  // per entry (NL): key, hash position, lowest index at the largest C, split sums
+  static constexpr size_t EK = align16(FI + 4 * TS);               // u64 key
+  static constexpr size_t EP = align16(EK + 8 * NL);               // u32 hash position
+  static constexpr size_t Gmin = align16(EP + 4 * NL);             // u32 lowest index
+  static constexpr size_t Acc = align16(Gmin + 4 * NL);            // u32[14][NL] split sums
+  static constexpr size_t Pid = align16(Acc + 14 * 4 * NL);        // u16[tile] gated pixels
+  static constexpr size_t Z = align16(Pid + 2 * Px);               // f32[tile] their depth
+  static constexpr size_t C = align16(Z + 4 * Px);                 // f32[tile] confidence
+  static constexpr size_t RGB = align16(C + 4 * Px);               // u32[tile] colour
+  static constexpr size_t PR = align16(RGB + 4 * Px);              // float4[K1][PrayPerView]
+  // dynamic shared memory of a launch with k1 neighbour views
+  static constexpr size_t smem(int k1) { return PR + 16 * (size_t)k1 * PrayPerView; }
+};
 constexpr unsigned kLoBits = 22;           // split of a <= 2^37 sum term: 512 lows fit in u32
 
 // Writes partial p as record pi and pushes it onto its cell's list; true when it is the
@@ -665,8 +674,9 @@ __device__ __forceinline__ ulonglong2 coarse_probe(const Tables& t, unsigned lon
   return __ldg(reinterpret_cast<const ulonglong2*>(&t.coarse[h]));
 }
 
-// Camera and first pixel of tile T: a division when every camera has the same size, else
-// a binary search of the per-camera tile ranges (constant bank).
+// Camera and first pixel of tile T (tiles of TH rows): a division when every camera has the
+// same size, else a binary search of the per-camera tile ranges (constant bank).
+template <int TH>
 __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, int& x0, int& y0) {
   if (ti.per_cam) {
     cam = T / ti.per_cam;
@@ -679,15 +689,23 @@ __device__ __forceinline__ void tile_of(const TileIndex& ti, int T, int& cam, in
   }
   const int local = T - ti.first[cam], tiles_x = (ti.W[cam] + kTileW - 1) / kTileW;
   x0 = (local % tiles_x) * kTileW;
-  y0 = (local / tiles_x) * kTileH;
+  y0 = (local / tiles_x) * TH;
 }
 
 // TOPK: the Sec. II.5(2)a variant; members are keyed and counted as usual, but a tile keeps
 // each cell's top-k members by C (packed (ordered(C) << 32) | ~g keys) instead of weights;
 // the consistency and weights of those members are computed per cell by k_reduce_topk.
-template <typename DT, bool TOPK, bool TRACE, int NB>
-__global__ void __launch_bounds__(kAssignThreads, kAssignBlocksPerSM)
+template <typename DT, bool TOPK, bool TRACE, int NB, int TH>
+__global__ void __launch_bounds__(AssignTile<TH>::Threads, AssignTile<TH>::BlocksPerSM)
 k_assign(const __grid_constant__ BatchArgs<NB> args) {
+  using AT = AssignTile<TH>;
+  constexpr int kTileH = TH, kTilePx = AT::Px, kAssignThreads = AT::Threads, kAssignWarps = AT::Warps;
+  constexpr int kAssignTS = AT::TS, kAssignNL = AT::NL, kPrayPerView = AT::PrayPerView;
+  constexpr int kConstWords = AT::ConstWords;
+  constexpr size_t kSmBC = AT::BC, kSmFK = AT::FK, kSmMinP = AT::MinP, kSmCmaxP = AT::CmaxP,
+                   kSmCntP = AT::CntP, kSmFI = AT::FI, kSmEK = AT::EK, kSmEP = AT::EP,
+                   kSmGmin = AT::Gmin, kSmAcc = AT::Acc, kSmPid = AT::Pid, kSmZ = AT::Z, kSmC = AT::C,
+                   kSmRGB = AT::RGB, kSmPR = AT::PR;
   int T;
   const FrameArgs& fa = args.f[batch_frame<NB>(args.tile_first, args.n, (int)blockIdx.x, T)];
   const RigDev* __restrict__ rigp = fa.rig;
@@ -717,7 +735,7 @@ k_assign(const __grid_constant__ BatchArgs<NB> args) {
 
   const RigDev& rig = *rigp;
   int cam, x0, y0;
-  tile_of(ti, T, cam, x0, y0);
+  tile_of<TH>(ti, T, cam, x0, y0);
   const int W = ti.W[cam], H = ti.H[cam], k1 = ti.k1;
   struct { int x0, y0; long long off; } td;
   td.x0 = x0;
@@ -727,7 +745,7 @@ k_assign(const __grid_constant__ BatchArgs<NB> args) {
   // warm L2 with the images of the tile that starts when this wave of blocks has finished
   if (threadIdx.x < 4 * kTileH && T + ti.ahead < t.n_tiles) {
     int pc, px0, py0;
-    tile_of(ti, T + ti.ahead, pc, px0, py0);
+    tile_of<TH>(ti, T + ti.ahead, pc, px0, py0);
     const int row = py0 + (threadIdx.x & (kTileH - 1)), kind = threadIdx.x / kTileH;
     if (row < ti.H[pc]) {                     // every address lies inside its image
       const long long li = (long long)row * ti.W[pc] + px0;
@@ -892,8 +910,8 @@ k_assign(const __grid_constant__ BatchArgs<NB> args) {
     int nview = 0, m = 0;
     if constexpr (!TOPK) {
       if (rig.use_cons && k1 > 0)
-        residual_sum<DT>(bc, k1, TilePairRays{reinterpret_cast<const float4*>(smem + kSmPR),
-                                              x - td.x0, y - td.y0},
+        residual_sum<DT>(bc, k1, TilePairRays<TH>{reinterpret_cast<const float4*>(smem + kSmPR),
+                                                  x - td.x0, y - td.y0},
                          rays, fp, z, sh, sl, nview);
       eh = joint_weight(rig, k1, sh, sl, c, mu[j], m);
     }
@@ -1906,6 +1924,19 @@ __global__ void __launch_bounds__(kThreads) k_screen_rows(ScreenArgs a) {
   store_row8<DT>(static_cast<DT*>(a.out[cam]) + (size_t)y * W + x0, o);
 }
 
+template <typename DT, int TH>
+cudaError_t set_assign_attributes_th() {
+  const int sm = (int)AssignTile<TH>::smem(kMaxK1);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false, 1, TH>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, true, 1, TH>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, 1, TH>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, true, 1, TH>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, false, kMaxBatch, TH>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, kMaxBatch, TH>, at, sm);
+  return e;
+}
+
 // Dynamic shared memory limit of the assign kernels for one depth type, set once per device
 // (the first call comes from context creation, outside any stream capture).  The attribute
 // call is idempotent, so two host threads that race here only repeat it.
@@ -1916,14 +1947,9 @@ cudaError_t set_assign_attributes() {
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
-  const int sm = (int)assign_smem(kMaxK1);
-  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_assign<DT, false, false, 1>, at, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, true, 1>, at, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, 1>, at, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, true, 1>, at, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, false, false, kMaxBatch>, at, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign<DT, true, false, kMaxBatch>, at, sm);
+  cudaError_t e = set_assign_attributes_th<DT, 8>();
+  if (e == cudaSuccess) e = set_assign_attributes_th<DT, 16>();
+  if (e == cudaSuccess) e = set_assign_attributes_th<DT, 32>();
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
   return e;
 }
@@ -1944,6 +1970,22 @@ cudaError_t launch_k(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, size
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// The assign step over the batch's tiles (TH rows a tile; the traced instantiation exists for
+// single frames only).
+template <typename DT, int NB, int TH>
+cudaError_t launch_assign(const BatchArgs<NB>& a, int n, bool top_k, bool traced, int max_k1, bool pdl,
+                          cudaStream_t s) {
+  const dim3 tiles(a.tile_first[n]), at(AssignTile<TH>::Threads);
+  const size_t sm = AssignTile<TH>::smem(top_k ? 0 : max_k1);
+  if constexpr (NB == 1) {
+    if (traced)
+      return top_k ? launch_k(pdl, k_assign<DT, true, true, NB, TH>, tiles, at, sm, s, a)
+                   : launch_k(pdl, k_assign<DT, false, true, NB, TH>, tiles, at, sm, s, a);
+  }
+  return top_k ? launch_k(pdl, k_assign<DT, true, false, NB, TH>, tiles, at, sm, s, a)
+               : launch_k(pdl, k_assign<DT, false, false, NB, TH>, tiles, at, sm, s, a);
 }
 
 // The frame kernels over n frames (NB = 1: one frame; NB = kMaxBatch: a batch of up to
@@ -1997,9 +2039,9 @@ cudaError_t launch_frames(const FrameLaunch* fr, int n, cudaStream_t s, cudaEven
   // also between the assign and reduce steps), never while stage events are recorded
   const bool pdl = pdl_level >= 1 && ev == nullptr;
   const bool pdl_reduce = pdl_level >= 2 && ev == nullptr;
-  const dim3 eb(emit, n), th(kThreads);
-  if ((err = launch_k(false, k_count<DT, NB>, dim3(a.count_first[n]), th, 0, s, a)) != cudaSuccess ||
-      (err = launch_k(pdl, k_levels<NB>, eb, th, 0, s, a)) != cudaSuccess)
+  const dim3 eb(emit, n), th3(kThreads);
+  if ((err = launch_k(false, k_count<DT, NB>, dim3(a.count_first[n]), th3, 0, s, a)) != cudaSuccess ||
+      (err = launch_k(pdl, k_levels<NB>, eb, th3, 0, s, a)) != cudaSuccess)
     return err;
   mark(2);
   bool traced = false;
@@ -2007,59 +2049,78 @@ cudaError_t launch_frames(const FrameLaunch* fr, int n, cudaStream_t s, cudaEven
     const TraceDev& tr = fr[f].tr;
     traced = traced || tr.pw || tr.omega || tr.e || tr.nview || tr.key;
   }
-  const dim3 tiles(a.tile_first[n]), at(kAssignThreads);
+  const int th = g0.tiles.th;
+  if (th == 8) err = launch_assign<DT, NB, 8>(a, n, g0.top_k != 0, traced, max_k1, pdl, s);
+  else if (th == 32) err = launch_assign<DT, NB, 32>(a, n, g0.top_k != 0, traced, max_k1, pdl, s);
+  else err = launch_assign<DT, NB, 16>(a, n, g0.top_k != 0, traced, max_k1, pdl, s);
+  if (err != cudaSuccess) return err;
+  mark(3);
   if (g0.top_k) {
-    if constexpr (NB == 1)
-      err = traced ? launch_k(pdl, k_assign<DT, true, true, NB>, tiles, at, assign_smem(0), s, a)
-                   : launch_k(pdl, k_assign<DT, true, false, NB>, tiles, at, assign_smem(0), s, a);
-    else
-      err = launch_k(pdl, k_assign<DT, true, false, NB>, tiles, at, assign_smem(0), s, a);
-    if (err != cudaSuccess) return err;
-    mark(3);
-    if ((err = launch_k(pdl_reduce, k_reduce_topk<DT, NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
+    if ((err = launch_k(pdl_reduce, k_reduce_topk<DT, NB>, eb, th3, 0, s, a)) != cudaSuccess) return err;
   } else {
-    const size_t sm = assign_smem(max_k1);
-    if constexpr (NB == 1)
-      err = traced ? launch_k(pdl, k_assign<DT, false, true, NB>, tiles, at, sm, s, a)
-                   : launch_k(pdl, k_assign<DT, false, false, NB>, tiles, at, sm, s, a);
-    else
-      err = launch_k(pdl, k_assign<DT, false, false, NB>, tiles, at, sm, s, a);
-    if (err != cudaSuccess) return err;
-    mark(3);
-    if ((err = launch_k(pdl_reduce, k_reduce<NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
+    if ((err = launch_k(pdl_reduce, k_reduce<NB>, eb, th3, 0, s, a)) != cudaSuccess) return err;
   }
   mark(4);
   if ((err = launch_k(pdl, k_scan<NB>, dim3(max_wblocks, n), dim3(1024), 0, s, a)) != cudaSuccess) return err;
   mark(5);
-  if ((err = launch_k(pdl, k_emit<NB>, eb, th, 0, s, a)) != cudaSuccess) return err;
+  if ((err = launch_k(pdl, k_emit<NB>, eb, th3, 0, s, a)) != cudaSuccess) return err;
   mark(6);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int assign_resident_blocks() { return kAssignBlocksPerSM; }
+namespace {
+template <int TH>
+int resident_th(int k1) {
+  static std::atomic<int> cache[kMaxK1 + 1];             // 0: not yet asked
+  k1 = std::max(0, std::min(k1, kMaxK1));
+  const int known = cache[k1].load(std::memory_order_relaxed);
+  if (known > 0) return known;
+  int n = 0;
+  const int sm = (int)AssignTile<TH>::smem(k1);
+  if (set_assign_attributes<uint16_t>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_assign<uint16_t, false, false, 1, TH>,
+                                                    AssignTile<TH>::Threads, sm) != cudaSuccess) {
+    cudaGetLastError();
+    return AssignTile<TH>::BlocksPerSM;
+  }
+  n = std::max(1, n);
+  cache[k1].store(n, std::memory_order_relaxed);
+  return n;
+}
+}  // namespace
 
-int fill_tile_index(const RigDev& rig, TileIndex* out) {
+int assign_resident_blocks(int th, int k1) {
+  return th == 8 ? resident_th<8>(k1) : th == 32 ? resident_th<32>(k1) : resident_th<16>(k1);
+}
+
+int retile(TileIndex* ti, int th) {
+  ti->th = th;
+  int n = 0;
+  for (int i = 0; i < ti->n_cams; ++i) {
+    ti->first[i] = n;
+    n += ((ti->W[i] + kTileW - 1) / kTileW) * ((ti->H[i] + th - 1) / th);
+  }
+  ti->first[ti->n_cams] = n;
+  bool same = true;
+  for (int i = 1; i < ti->n_cams; ++i) same = same && ti->W[i] == ti->W[0] && ti->H[i] == ti->H[0];
+  ti->per_cam = same && ti->n_cams > 0 ? ti->first[1] : 0;
+  return n;
+}
+
+int fill_tile_index(const RigDev& rig, TileIndex* out, int th) {
   memset(out, 0, sizeof(*out));
   out->n_cams = rig.n_cams;
   out->k1 = rig.k1;
-  int n = 0;
   for (int i = 0; i < rig.n_cams; ++i) {
-    out->first[i] = n;
     out->W[i] = rig.cam[i].W;
     out->H[i] = rig.cam[i].H;
     out->off[i] = rig.cam[i].off;
     out->pray[i] = rig.k1 > 0 ? rig.pair[rig.cam[i].pair0].ga : 0;
-    n += ((rig.cam[i].W + kTileW - 1) / kTileW) * ((rig.cam[i].H + kTileH - 1) / kTileH);
   }
-  out->first[rig.n_cams] = n;
-  bool same = true;
-  for (int i = 1; i < rig.n_cams; ++i)
-    same = same && rig.cam[i].W == rig.cam[0].W && rig.cam[i].H == rig.cam[0].H;
-  out->per_cam = same && rig.n_cams > 0 ? out->first[1] : 0;
   out->ahead = kNoPrefetch;                      // no prefetch unless the caller sets it
-  return n;
+  return retile(out, th);
 }
 
 void fill_block_consts(const RigDev& rig, BlockConst* out) {
@@ -2154,7 +2215,8 @@ cudaError_t launch_frame(const RigDev* rig, const float2* rays, const FramePtrs&
 cudaError_t launch_batch(const FrameLaunch* frames, int n, cudaStream_t s) {
   if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
   for (int f = 1; f < n; ++f)                       // one depth type and one fusion variant
-    if (frames[f].geo->depth_f32 != frames[0].geo->depth_f32 || frames[f].geo->top_k != frames[0].geo->top_k)
+    if (frames[f].geo->depth_f32 != frames[0].geo->depth_f32 || frames[f].geo->top_k != frames[0].geo->top_k ||
+        frames[f].geo->tiles.th != frames[0].geo->tiles.th)
       return cudaErrorInvalidValue;
   if (frames[0].geo->depth_f32) return launch_frames<float, kMaxBatch>(frames, n, s, nullptr);
   return launch_frames<uint16_t, kMaxBatch>(frames, n, s, nullptr);

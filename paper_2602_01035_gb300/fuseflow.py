@@ -82,11 +82,12 @@ class fuseflow_host_cloud(C.Structure):
 
 class fuseflow_tuning(C.Structure):
     _fields_ = [("count_chunks", C.c_int32), ("emit_blocks", C.c_int32),
-                ("prefetch_tiles", C.c_int32), ("programmatic", C.c_int32)]
+                ("prefetch_tiles", C.c_int32), ("programmatic", C.c_int32), ("tile_h", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {"count_chunks": self.count_chunks, "emit_blocks": self.emit_blocks,
-                "prefetch_tiles": self.prefetch_tiles, "programmatic": self.programmatic}
+                "prefetch_tiles": self.prefetch_tiles, "programmatic": self.programmatic,
+                "tile_h": self.tile_h}
 
 
 class fuseflow_server_stats(C.Structure):
@@ -457,9 +458,10 @@ def fuseflow_get_tuning(ctx) -> fuseflow_tuning:
 
 
 def fuseflow_set_tuning(ctx, count_chunks: int, emit_blocks: int, prefetch_tiles: int,
-                        programmatic: int = 0) -> int:
-    """Status of replacing the context's launch geometry (INVALID_ARG leaves it unchanged)."""
-    tu = fuseflow_tuning(count_chunks, emit_blocks, prefetch_tiles, programmatic)
+                        programmatic: int = 0, tile_h: int = 0) -> int:
+    """Status of replacing the context's launch geometry (INVALID_ARG leaves it unchanged;
+    tile_h 0 keeps the current tile height)."""
+    tu = fuseflow_tuning(count_chunks, emit_blocks, prefetch_tiles, programmatic, tile_h)
     return load().fuseflow_set_tuning(ctx, C.byref(tu))
 
 
@@ -643,9 +645,9 @@ class FuseFlow:
         return fuseflow_get_tuning(self.ctx).as_dict()
 
     def set_tuning(self, count_chunks: int, emit_blocks: int, prefetch_tiles: int,
-                   programmatic: int = 0):
+                   programmatic: int = 0, tile_h: int = 0):
         _check(fuseflow_set_tuning(self.ctx, count_chunks, emit_blocks, prefetch_tiles,
-                                   programmatic), "fuseflow_set_tuning")
+                                   programmatic, tile_h), "fuseflow_set_tuning")
 
     def set_trace(self, **arrays):
         fuseflow_set_trace(self.ctx, **{k: (v.data_ptr() if v is not None else 0)
