@@ -411,6 +411,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
   static_assert(TS % kThreads == 0 && kThreads % 32 == 0 && TS <= 65536, "block table shape");
   __shared__ unsigned s_nocc;
   __shared__ unsigned s_red[kThreads / 32][9];
+  // per warp, the runs its lanes send to the block table in a chunk (at most one per run,
+  // kCountPx a lane), inserted by the whole warp at once; the counts share the storage of
+  // s_occ, which only the final flush uses
+  constexpr int kRunCap = 32 * kCountPx;
+  static_assert((kThreads / 32) * kRunCap <= TS, "run counts fit in s_occ");
+  __shared__ unsigned long long s_mk[kThreads / 32][kRunCap];
+  unsigned short* const s_mn = s_occ + (threadIdx.x >> 5) * kRunCap;
+  __shared__ unsigned s_mcount[kThreads / 32];
   const RigDev& rig = *rigp;
   // the camera's constants and the rig's scalars in registers (they would otherwise be
   // re-read for every pixel, as the atomics below may alias memory for the compiler)
@@ -423,6 +431,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
   const bool idle = c0 * kCountBlockPx >= npx;                  // uniform over the block
   for (int i = threadIdx.x; i < TS; i += kThreads) { s_key[i] = kKeyEmpty; s_cnt[i] = 0; }
   if (threadIdx.x == 0) { s_fill = 0u; s_nocc = 0u; }
+  if (threadIdx.x < kThreads / 32) s_mcount[threadIdx.x] = 0u;
   __syncthreads();
 
   const DT* __restrict__ dep = static_cast<const DT*>(fp.depth[cam]);
@@ -444,8 +453,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
     if (pc < npx) load8<DT>(dep, cf, pc, npx, dcur, ccur);
     pn = pc + kCountBlockPx;
     // Sec. II.5(1)c density estimate. Runs of equal coarse cells along the thread's
-    // pixels: the first run (if the thread has several) and the last run are kept, the
-    // ones between go to the block table at once (rare: a cell spans ~70 pixels here).
+    // pixels: the first run (if the thread has several) and the last run are kept for the
+    // merge along the warp, the ones between are staged for the warp's insertion pass (a
+    // block-table insertion in the unrolled loop itself would run once per unrolled pixel
+    // for the whole warp whenever any lane ends a run there).
     unsigned long long khead = kKeyEmpty, ktail = kKeyEmpty;
     unsigned nhead = 0u, run = 0u, nruns = 0u;
     int cx = 0, cy = 0, cz = 0;
@@ -503,7 +514,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
             khead = pack_key(0, cx, cy, cz);
             nhead = run;
           } else {
-            count_add<TS>(t, s_key, s_cnt, &s_fill, pack_key(0, cx, cy, cz), run);
+            const unsigned q = atomicAdd(&s_mcount[warp], 1u);
+            s_mk[warp][q] = pack_key(0, cx, cy, cz);
+            s_mn[q] = (unsigned short)run;
           }
         }
         if (counted) {
@@ -536,8 +549,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_count(const __grid_constant__ B
           start = start || f2;
         }
       }
-      if (nruns >= 2u && !cont) count_add<TS>(t, s_key, s_cnt, &s_fill, khead, nhead);
-      if (ktail != kKeyEmpty && (lane == 31 || nstart)) count_add<TS>(t, s_key, s_cnt, &s_fill, ktail, v);
+      // the lane's first run unless it continues the previous lane's chain, and its last
+      // run where a chain ends, join the middle runs; then every run of the warp goes to
+      // the block table, one lane each
+      if (nruns >= 2u && !cont) {
+        const unsigned q = atomicAdd(&s_mcount[warp], 1u);
+        s_mk[warp][q] = khead;
+        s_mn[q] = (unsigned short)nhead;
+      }
+      if (ktail != kKeyEmpty && (lane == 31 || nstart)) {
+        const unsigned q = atomicAdd(&s_mcount[warp], 1u);
+        s_mk[warp][q] = ktail;
+        s_mn[q] = (unsigned short)v;
+      }
+      __syncwarp();
+      const unsigned nm = s_mcount[warp];
+      for (unsigned q = lane; q < nm; q += 32u) count_add<TS>(t, s_key, s_cnt, &s_fill, s_mk[warp][q], s_mn[q]);
+      __syncwarp();
+      if (lane == 0) s_mcount[warp] = 0u;
+      __syncwarp();
     }
     x += kCountBlockPx;                                           // next chunk's first pixel
     while (x >= C.W) { x -= C.W; ++y; }
