@@ -340,7 +340,7 @@ __device__ __forceinline__ void load8(const DT* __restrict__ d, const float* __r
   const bool full = p0 + 7 < npx;
   if constexpr (sizeof(DT) == 2) {
     if (full && ((reinterpret_cast<uintptr_t>(d + p0) & 15) == 0)) {
-      const uint4 u = __ldcs(reinterpret_cast<const uint4*>(d + p0));
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(d + p0));
       const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
       for (int k = 0; k < 4; ++k) { dv[2 * k] = (DT)(w[k] & 0xffff); dv[2 * k + 1] = (DT)(w[k] >> 16); }
@@ -350,8 +350,8 @@ __device__ __forceinline__ void load8(const DT* __restrict__ d, const float* __r
     }
   } else {
     if (full && ((reinterpret_cast<uintptr_t>(d + p0) & 15) == 0)) {
-      const float4 f0 = __ldcs(reinterpret_cast<const float4*>(d + p0));
-      const float4 f1 = __ldcs(reinterpret_cast<const float4*>(d + p0) + 1);
+      const float4 f0 = __ldg(reinterpret_cast<const float4*>(d + p0));
+      const float4 f1 = __ldg(reinterpret_cast<const float4*>(d + p0) + 1);
       dv[0] = f0.x; dv[1] = f0.y; dv[2] = f0.z; dv[3] = f0.w;
       dv[4] = f1.x; dv[5] = f1.y; dv[6] = f1.z; dv[7] = f1.w;
     } else {
@@ -360,8 +360,8 @@ __device__ __forceinline__ void load8(const DT* __restrict__ d, const float* __r
     }
   }
   if (full && ((reinterpret_cast<uintptr_t>(c + p0) & 15) == 0)) {
-    const float4 f0 = __ldcs(reinterpret_cast<const float4*>(c + p0));
-    const float4 f1 = __ldcs(reinterpret_cast<const float4*>(c + p0) + 1);
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(c + p0));
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(c + p0) + 1);
     cv[0] = f0.x; cv[1] = f0.y; cv[2] = f0.z; cv[3] = f0.w;
     cv[4] = f1.x; cv[5] = f1.y; cv[6] = f1.z; cv[7] = f1.w;
   } else {
