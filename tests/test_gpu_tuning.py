@@ -149,6 +149,19 @@ def test_a_batch_needs_one_tile_height(ffmod):
             b.set_tuning(tu["count_chunks"], tu["emit_blocks"], tu["prefetch_tiles"], tu["programmatic"], 16)
             assert batch.fuse([(d, c, r), (d, c, r)]) == ffmod.FUSEFLOW_OK
             torch.cuda.synchronize()
+            # at another common height the batch gives each context's own result bitwise
+            for x in (a, b):
+                x.set_tuning(tu["count_chunks"], tu["emit_blocks"], tu["prefetch_tiles"], tu["programmatic"], 32)
+            alone = run_gpu(a, fr, torch, with_trace=False)
+            assert batch.fuse([(d, c, r), (d, c, r)]) == ffmod.FUSEFLOW_OK
+            torch.cuda.synchronize()
+            for x in (a, b):
+                status, st = x.stats(check=False)
+                assert status == ffmod.FUSEFLOW_OK and st.as_dict() == alone["stats"]
+                cloud = ffmod.fuseflow_get_cloud(x.ctx)
+                got = {k: v.cpu().numpy() for k, v in x.cloud_tensors(cloud, int(st.n_cells)).items()}
+                for k in ("pos", "rgb", "weight", "count", "rep", "key"):
+                    assert np.array_equal(got[k].view(alone["cells"][k].dtype), alone["cells"][k]), k
         finally:
             batch.close()
     finally:
