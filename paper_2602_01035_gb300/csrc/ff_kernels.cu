@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const __grid_constant__ Bat
 // scaled by the largest).  Members are counted over the whole cell; the representative is
 // the cell's top member.
 template <typename DT, int NB>
-__global__ void __launch_bounds__(kThreads) k_reduce_topk(const __grid_constant__ BatchArgs<NB> args) {
+__global__ void __launch_bounds__(kThreads, 3) k_reduce_topk(const __grid_constant__ BatchArgs<NB> args) {
   const FrameArgs& fa = args.f[batch_frame_y<NB>()];
   const RigDev* __restrict__ rigp = fa.rig;
   const float2* __restrict__ rays = fa.rays;
